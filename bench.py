@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of one PP-PC iteration (the whole hot path: batched fine
+propagators, jumps, coarse linearisation, time-axis DFT, harmonic solves,
+inverse DFT + update) on the medium coax workload: 19 801 DOFs, N = 64
+subintervals, 50 implicit-Euler steps each, Brauer steel sheath with
+sigma = 2e7 S/m, 10 A at 50 Hz.
+
+A "step" is one pppc_iterate() call.  value = fine DOF-steps per second
+(N * n_fine * ndof per step) over the timed steps, device time from CUDA
+events on the library's stream; L2 is flushed (512 MB write) between steps.
+Also reported: the time to periodic steady state at rel_res 1e-8 from U = 0,
+the e2e rate through the C ABI with host buffers, the roofline of the fine
+propagator kernel, and the CPU oracle on a bounded sample.
+
+Multi-GPU: the method runs on one GPU; with --gpus N each rank runs an
+independent replica (weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s to periodic steady state at rel res 1e-8; fine DOF-steps/s; HBM % of peak"
+UNIT = "fine DOF-steps/s"
+WORKLOAD = "medium"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady-state run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 rate of a GB300 (recipe figure); the FP64 path is bound by it.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB: int) -> float:
+    """Algorithmic bytes of one PCG iteration per (row, lane) of the fine
+    propagator (single-reduction CG, two phases): phase A reads z, r and
+    writes w; phase B reads z, w, p, s, r, u and writes p, s, r, z, u.  Vectors
+    are FP32 in the mixed path (u stays FP64).  Matrix: per-lane values on the
+    special rows, shared values and column indices amortised over the lanes."""
+    v = 4.0 if mixed else 8.0
+    phase_a = 3 * v
+    phase_b = 5 * v + 8.0 + 4 * v + 8.0
+    diag = special_frac * v + (1 - special_frac) * v / NB
+    matrix = special_frac * nnz_row * v + (1 - special_frac) * nnz_row * (v + 4.0) / NB \
+        + special_frac * nnz_row * 4.0 / NB
+    return phase_a + phase_b + diag + matrix
+
+
+def cpu_baseline(prob, max_seconds=20.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    fine propagators of whole subintervals from rest (Eqs. 2-3)."""
+    import numpy as np
+
+    from oracle.fem import FEModel
+    from oracle.stepping import propagate
+
+    m = FEModel(prob)
+    steps = 0
+    t0 = time.perf_counter()
+    n = 1
+    while True:
+        propagate(m, n, np.zeros(m.ndof), prob.N, prob.n_fine, prob.T)
+        steps += prob.n_fine
+        n += 1
+        el = time.perf_counter() - t0
+        if el > max_seconds * 0.5 or n > prob.N:
+            break
+    return {"value": steps * m.ndof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n - 1} subinterval(s) x {prob.n_fine} implicit-Euler/Newton steps with sparse LU, "
+                      f"{m.ndof} DOFs, from rest ({el:.1f} s)"}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle timed as it stands (rank 0 only)."""
+    if rank != 0:
+        return
+    from synth import workload
+
+    prob = workload(WORKLOAD)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t_all = time.perf_counter()
+    base = None
+    for _ in range(max(1, args.steps)):
+        base = cpu_baseline(prob, max_seconds=min(20.0, 120.0 / max(1, args.steps)))
+        vals.append(base["value"])
+    value = statistics.median(vals)
+    base["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "coax medium: nr=100 x ntheta=200 (19801 DOFs), N=64, 50 fine steps, "
+                                   "sigma=2e7, Brauer steel, 10 A 50 Hz", "parallelism": "replicas only"},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1905_13076_gb300 import from_problem
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prob = workload(WORKLOAD)
+    mixed = args.precision == "mixed"
+    solver = from_problem(prob, precision=args.precision, stream=stream)
+    ndof = solver.ndof
+    units_per_step = prob.N * prob.n_fine * ndof
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # ---- warm-up (also the first PP-PC iterations from U = 0)
+    solver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
+    for _ in range(max(3, args.warmup)):
+        solver.iterate()
+
+    # ---- timed region: K iterations, L2 flushed between them
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fine_ms, pcg, newton, launches = [], 0, 0, 0
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[k][0].record(stream)
+            solver.iterate()
+            ev[k][1].record(stream)
+            st = solver.stats()
+            fine_ms.append(st["fine_ms"])
+            pcg += st["pcg_iters"]
+            newton += st["newton_iters"]
+            launches += st["launches"]
+        torch.cuda.synchronize(dev)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t_max = total_ms
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = units_per_step * args.steps * world / (t_max * 1e-3)
+
+    # ---- roofline of the fine-propagator kernel (the dominant kernel)
+    mc = solver.mesh_counts()
+    nnz_row = mc["nnz"] / mc["ndof"]
+    sp_frac = mc["special_rows"] / mc["ndof"]
+    bpr = pcg_bytes_per_row_lane(mixed, sp_frac, nnz_row, prob.N)
+    fine_s = sum(fine_ms) * 1e-3
+    pcg_bytes = bpr * ndof * prob.N * pcg
+    hbm_peak, peak_src = peaks()
+    if mixed:
+        achieved = pcg_bytes / fine_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "kernel": "fine_sweep_kernel<float>"}
+    else:
+        flops_row = 2 * nnz_row + 6 + 9
+        achieved = flops_row * ndof * prob.N * pcg / fine_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "peak_source": "recipe FP64 rate",
+                "kernel": "fine_sweep_kernel<double>", "hbm_gbs_equiv": pcg_bytes / fine_s / 1e9}
+
+    # ---- end to end through the C ABI with host buffers
+    pinned = torch.zeros((prob.N, prob.mesh.n_nodes), dtype=torch.float64).pin_memory()
+    U_host = pinned.numpy()
+    U_host[:] = solver.get_state()
+    e2e_times = []
+    for k in range(args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        solver.set_state(U_host)
+        solver.iterate()
+        U_host[:] = solver.get_state()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = units_per_step * args.steps * world / sum(e2e_times)
+    state_bytes = prob.N * prob.mesh.n_nodes * 8
+
+    # ---- time to periodic steady state from U = 0
+    tts = None
+    if not args.no_tts:
+        solver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        iters, rr = solver.solve_periodic(tol=1e-8, kmax=60, raise_on_fail=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st = solver.stats()
+        tts = {"seconds": e0.elapsed_time(e1) * 1e-3, "host_seconds": time.perf_counter() - t0,
+               "pppc_iterations": iters, "rel_res": rr, "newton_iters": st["newton_iters"],
+               "pcg_iters": st["pcg_iters"], "cocg_iters": st["cocg_iters"]}
+
+    if rank != 0:
+        solver.close()
+        return
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(prob)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": "coax medium: nr=100 x ntheta=200 (19801 DOFs), N=64, 50 fine steps, "
+                               "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
+                   "parallelism": "replicas only", "l2": "flushed between steps (512 MB write)"},
+        "time_to_steady_state": tts,
+        "per_step": {"pcg_iters": pcg / args.steps, "newton_iters": newton / args.steps,
+                     "fine_ms": sum(fine_ms) / args.steps, "step_ms": step_ms},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    solver.close()
+
+
+if __name__ == "__main__":
+    main()

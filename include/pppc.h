@@ -1,0 +1,219 @@
+/*
+ * pppc.h -- C ABI of the GB300 library for the periodic eddy-current problem
+ *
+ *     M du/dt + K(u) u = f(t),  t in (0, T),   u(0) = u(T)        (Sec. 2, Eq. 1)
+ *
+ * solved by the periodic Parareal algorithm with a periodic coarse problem
+ * (PP-PC, Eq. 4) whose block-cyclic coarse system (Eqs. 9-10) is solved
+ * harmonic by harmonic after a discrete Fourier transform along the time
+ * axis (Sec. 3, Eqs. 11-14).
+ *
+ * Conventions shared by every call
+ *  - All calls return a pppc_status; nothing throws across the ABI.  After a
+ *    failure, pppc_last_error(h) holds a one-line reason.
+ *  - All device work is ordered on the stream given in pppc_config.stream
+ *    (a cudaStream_t; NULL means the legacy default stream).  Calls that
+ *    return scalars (iterate, solve_periodic, propagate_fine, coarse_update)
+ *    synchronise that stream before returning.
+ *  - A handle is not thread-safe; separate handles are independent.
+ *  - States are FP64, laid out subinterval-major over ALL mesh nodes:
+ *    U[n * n_nodes + i] is node i at the coarse point T_n = n T / N,
+ *    n = 0..N-1.  Dirichlet nodes are ignored on input and returned as 0.
+ *  - "on_device" != 0 means the pointer is CUDA device memory valid on the
+ *    handle's stream; 0 means host memory (copied inside the call).  The
+ *    caller owns every buffer it passes; the library keeps no pointer to it
+ *    after the call returns.
+ *  - The handle owns all device workspace; it is allocated by
+ *    pppc_set_mesh and released by pppc_destroy.
+ */
+#ifndef PPPC_H
+#define PPPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pppc_status {
+    PPPC_OK = 0,
+    PPPC_ERR_INVALID_ARG = 1,   /* bad pointer, size, index, degenerate triangle ... */
+    PPPC_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in last_error) */
+    PPPC_ERR_STATE = 3,         /* call out of order (e.g. no mesh or source yet) */
+    PPPC_ERR_NEWTON = 4,        /* a fine-step Newton iteration hit max_newton */
+    PPPC_ERR_LINEAR = 5,        /* PCG or COCG hit its iteration cap */
+    PPPC_ERR_BREAKDOWN = 6,     /* PCG/COCG breakdown (zero or non-positive curvature) */
+    PPPC_ERR_NAN = 7,           /* a non-finite residual appeared */
+    PPPC_ERR_TIMEOUT = 8,       /* a device-side grid barrier gave up waiting */
+    PPPC_ERR_NOT_CONVERGED = 9, /* solve_periodic reached kmax; state kept, resumable */
+    PPPC_ERR_UNSUPPORTED = 10,  /* valid request this build does not provide */
+    PPPC_ERR_NOMEM = 11         /* device allocation failed */
+} pppc_status;
+
+typedef enum pppc_precision {
+    PPPC_FP64 = 0,   /* every operation in FP64 */
+    PPPC_MIXED = 1   /* FP32 fine PCG; FP64 Newton residual, jumps, DFT, COCG, update */
+} pppc_precision;
+
+typedef enum pppc_coarse_lin {
+    /* The paper leaves the coarse matrix of the nonlinear case open (end of
+     * Sec. 2).  Within iteration k the coarse stiffness Kbar is frozen as: */
+    PPPC_COARSE_AVG_JACOBIAN = 0, /* (1/N) sum_n dK(U)U/dU at U = U_n^k  (default) */
+    PPPC_COARSE_AVG_CHORD = 1,    /* (1/N) sum_n K(U_n^k) */
+    PPPC_COARSE_ZERO_FIELD = 2    /* dK(U)U/dU at U = 0 */
+} pppc_coarse_lin;
+
+typedef enum pppc_nu_model {
+    PPPC_NU_LINEAR = 0,  /* constant reluctivity nu */
+    PPPC_NU_BRAUER = 1   /* nu(B^2) = k1 exp(k2 B^2) + k3 */
+} pppc_nu_model;
+
+/* Material of one region (index = value in the region[] array). */
+typedef struct pppc_material {
+    double sigma;       /* conductivity [S/m]; > 0 puts the region into M */
+    int32_t nu_model;   /* pppc_nu_model */
+    double nu;          /* reluctivity [m/H] for PPPC_NU_LINEAR, > 0 */
+    double k1, k2, k3;  /* Brauer constants for PPPC_NU_BRAUER, k1,k3 > 0, k2 >= 0 */
+    int32_t is_source;  /* 1: carries the impressed current I(t) uniformly */
+} pppc_material;
+
+/* Opaque handle: one problem (mesh, materials, source, time grid, state). */
+typedef struct pppc_handle pppc_handle;
+
+typedef void* (*pppc_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*pppc_free_fn)(void* ptr, void* ctx);
+
+typedef struct pppc_config {
+    double T;             /* period [s], > 0 */
+    int32_t N;            /* subintervals [T_{n-1}, T_n], even, 2..1024 */
+    int32_t n_fine;       /* implicit-Euler steps per subinterval, >= 1 */
+    int32_t precision;    /* pppc_precision */
+    int32_t coarse_lin;   /* pppc_coarse_lin */
+    double tol_newton;    /* fine Newton stop: ||R||_2 <= tol_newton * ||g||_2 * sum_j |amp_j| */
+    int32_t max_newton;   /* Newton iteration cap per fine step */
+    double tol_lin;       /* PCG: ||r|| <= max(tol_lin, 0.1 * Newton stop / ||R||) * ||R|| */
+    int32_t max_lin;      /* PCG iteration cap per Newton iteration */
+    double tol_coarse;    /* COCG: ||r_p|| <= tol_coarse * ||b_p|| per harmonic */
+    int32_t max_coarse;   /* COCG iteration cap */
+    void* stream;         /* cudaStream_t; NULL = legacy default stream */
+    pppc_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc) */
+    pppc_free_fn free_fn; /* matching free (NULL: cudaFree) */
+    void* alloc_ctx;      /* passed to alloc/free_fn */
+} pppc_config;
+
+/* Iteration counts of the most recent iterate / solve / propagate call. */
+typedef struct pppc_stats {
+    int64_t newton_iters;    /* Newton iterations, summed over steps (max over lanes per step) */
+    int64_t pcg_iters;       /* PCG iterations, summed over Newton iterations (lockstep) */
+    int64_t cocg_iters;      /* COCG iterations of the coarse solves (lockstep over harmonics) */
+    int64_t fine_steps;      /* implicit-Euler steps per lane */
+    int32_t pppc_iters;      /* completed PP-PC updates */
+    double rel_res;          /* last ||d|| / ||F|| */
+    double fine_ms;          /* device time of the fine-propagator launches (CUDA events) */
+    double coarse_ms;        /* device time of the coarse kernels (jumps .. update) */
+    int64_t launches;        /* kernels this library launched during the call */
+} pppc_stats;
+
+/* Fill *cfg with defaults: T=0.02, N=16, n_fine=20, FP64, averaged Jacobian,
+ * tol_newton=1e-10, max_newton=30, tol_lin=1e-6, max_lin=20000,
+ * tol_coarse=1e-10, max_coarse=20000, default stream, cudaMalloc. */
+void pppc_config_default(pppc_config* cfg);
+
+/* Create a handle for the time grid of Sec. 2: N subintervals of length
+ * dT = T/N (the coarse step, Eq. 8), each marched with n_fine implicit-Euler
+ * fine steps of dt = T/(N n_fine) (Eq. 3).  *out is NULL on error.
+ * Errors: INVALID_ARG (null pointer, N odd or out of range, T <= 0, ...). */
+pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out);
+
+/* Release the handle and all its device memory.  NULL is a no-op. */
+void pppc_destroy(pppc_handle* h);
+
+/* Upload the mesh and materials of the space discretisation of Eq. 1
+ * (linear triangles, nodal A_z): xy[2*n_nodes] coordinates [m];
+ * tri[3*n_tri] node indices; region[n_tri] in [0, n_regions);
+ * dirichlet[n_nodes] (1 = A fixed to 0); mat[n_regions].  Builds the sparse
+ * pattern and element maps on the host and the matrices K_lin, M and the
+ * source shape g on the device.  Host arrays are only read during the call.
+ * Resets the state to U = 0.
+ * Errors: INVALID_ARG (index out of range, zero-area triangle, nu <= 0, no
+ * free node, no source region), NOMEM, CUDA. */
+pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int32_t n_tri,
+                          const int32_t* tri, const int32_t* region, const uint8_t* dirichlet,
+                          int32_t n_regions, const pppc_material* mat);
+
+/* Impressed current of the source regions (the excitation f of Eq. 1):
+ * I(t) = sum_j amp[j] sin(2 pi freq[j] t + phase[j]), spread uniformly over
+ * the discrete source area so that the nodal source sums to I(t).
+ * Errors: INVALID_ARG if n_harm < 1 or some freq[j] * T is not an integer
+ * (f must be T-periodic, Eq. 1); STATE before set_mesh. */
+pppc_status pppc_set_source(pppc_handle* h, int32_t n_harm, const double* amp, const double* freq,
+                            const double* phase);
+
+/* Set / read the PP-PC state U_0..U_{N-1} (layout above). */
+pppc_status pppc_set_state(pppc_handle* h, const double* U, int32_t on_device);
+pppc_status pppc_get_state(pppc_handle* h, double* U, int32_t on_device);
+
+/* All N fine propagators at once (Eqs. 2-3): F[j] = F_{j+1}(U[j]) for
+ * j = 0..N-1, i.e. subinterval j+1 marched from U_j at T_j to T_{j+1}.
+ * U and F use the state layout; they may not alias.  Does not change the
+ * handle's state.  Errors: NEWTON, LINEAR, BREAKDOWN, NAN, TIMEOUT, CUDA. */
+pppc_status pppc_propagate_fine(pppc_handle* h, const double* U, double* F, int32_t on_device);
+
+/* The coarse part of one PP-PC iteration (Eq. 4 with the implicit-Euler
+ * coarse propagator of Eq. 8, solved through Eqs. 9-14): given U^k and the
+ * fine values F[j] = F_{j+1}(U^k_j), write U^{k+1} to U_new and
+ * ||d|| / ||F|| of U^k (d_n = F_n - U_{n mod N}) to *rel_res (may be NULL).
+ * Does not change the handle's state.  Errors: LINEAR, BREAKDOWN, TIMEOUT,
+ * CUDA. */
+pppc_status pppc_coarse_update(pppc_handle* h, const double* U, const double* F, double* U_new,
+                               double* rel_res, int32_t on_device);
+
+/* One PP-PC iteration (Eq. 4) on the handle's state: U^k -> U^{k+1}.
+ * *rel_res (may be NULL) receives ||d|| / ||F|| of the incoming U^k. */
+pppc_status pppc_iterate(pppc_handle* h, double* rel_res);
+
+/* Iterate until rel_res(U^k) <= tol or kmax updates are done.  On success
+ * the state is the first U^k that passed and *iters = k (the number of
+ * completed updates).  Errors: NOT_CONVERGED (state = U^kmax, resumable),
+ * and those of pppc_iterate.  iters and rel_res may be NULL. */
+pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_t* iters,
+                                double* rel_res);
+
+/* Iteration counts of the last propagate / coarse / iterate / solve call. */
+pppc_status pppc_get_stats(pppc_handle* h, pppc_stats* out);
+
+/* Newton trace of the fine propagators (diagnostics).  pppc_set_trace(h, cap)
+ * with cap > 0 makes every later fine sweep record up to cap records of
+ * 5 doubles: {fine step, Newton iteration, max over subintervals of ||R||_2,
+ * subintervals still iterating, PCG iterations of the preceding solve};
+ * cap = 0 turns it off.  pppc_get_trace copies at most cap records of the
+ * last sweep into out[5*cap] (host memory) and stores the number recorded
+ * (which may exceed cap) in *n.  Errors: INVALID_ARG, STATE, NOMEM. */
+pppc_status pppc_set_trace(pppc_handle* h, int32_t cap);
+pppc_status pppc_get_trace(pppc_handle* h, double* out, int32_t cap, int32_t* n);
+
+/* Number of free nodes (degrees of freedom) after Dirichlet elimination. */
+int32_t pppc_ndof(pppc_handle* h);
+
+/* Sizes of the assembled system (for roofline accounting). */
+typedef struct pppc_mesh_counts {
+    int64_t ndof;             /* free nodes */
+    int64_t nnz;              /* entries of the sparse pattern */
+    int64_t special_rows;     /* rows touching a nonlinear or conductive element */
+    int64_t special_entries;  /* entries of those rows (values stored per lane) */
+    int64_t nonlinear_elems;  /* triangles with the Brauer law */
+} pppc_mesh_counts;
+pppc_status pppc_get_mesh_counts(pppc_handle* h, pppc_mesh_counts* out);
+
+/* One-line description of the last error on h (owned by h), or of the last
+ * pppc_create failure when h is NULL. */
+const char* pppc_last_error(pppc_handle* h);
+
+/* Static name of a status code. */
+const char* pppc_status_string(pppc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPPC_H */

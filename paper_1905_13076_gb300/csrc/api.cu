@@ -1,0 +1,768 @@
+// C ABI of the library (include/pppc.h): handle, mesh upload, and the PP-PC
+// driver that sequences the kernels of one iteration (Sec. 2, Eq. 4; Sec. 3).
+// There is no CPU fallback: every floating-point step of the method runs in
+// the kernels of setup.cu, fine.cu and coarse.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pppc.h"
+#include "args.h"
+#include "kernels.h"
+#include "mesh_host.h"
+
+using namespace pppc;
+
+namespace {
+thread_local std::string g_create_error;
+// Smallest relative residual asked of an FP32 PCG/COCG solve (mixed precision).
+constexpr double kFp32KrylovFloor = 1e-6;
+}
+
+struct pppc_handle {
+    pppc_config cfg{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    bool has_mesh = false, has_source = false;
+    int N = 0, NB = 0, H = 0;
+    double dt = 0.0, dT = 0.0;
+    bool fp32 = false;
+    HostMesh hm;
+    std::vector<void*> allocs;   // everything allocated for the current mesh
+    MeshDev md{};
+    int* d_node_of_dof = nullptr;
+    int* d_dof_of_node = nullptr;
+    // lane vectors [ndof][NB]
+    double *U = nullptr, *Unext = nullptr, *F = nullptr, *uprev = nullptr, *d = nullptr;
+    double* elem = nullptr;
+    void *r = nullptr, *z = nullptr, *w = nullptr, *p = nullptr, *s = nullptr, *J = nullptr, *invd = nullptr;
+    // coarse
+    double *y = nullptr, *b = nullptr, *Kbar = nullptr, *tw = nullptr;
+    void *cx = nullptr, *cr = nullptr, *cz = nullptr, *cw = nullptr, *cp = nullptr, *cs = nullptr, *cinvd = nullptr;
+    // reductions and control
+    double *part = nullptr, *sums = nullptr, *jsums = nullptr, *scalars = nullptr;
+    GridBarrier* bar = nullptr;
+    int* status = nullptr;
+    long long* counters = nullptr;
+    double* ext = nullptr;   // [N][n_nodes] staging for host states
+    double* trace = nullptr; // Newton trace of the fine sweep (optional)
+    int* trace_len = nullptr;
+    int trace_cap = 0;
+    LaunchCfg fine_cfg, cocg_cfg;
+    bool coarse_fp32 = false;       // the harmonic solves run in FP64 in both precisions
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    SourceDev src{};
+    double gnorm = 0.0, src_area = 0.0;
+    pppc_stats stats{};
+};
+
+namespace {
+
+const char* kStatusNames[] = {"PPPC_OK",
+                              "PPPC_ERR_INVALID_ARG",
+                              "PPPC_ERR_CUDA",
+                              "PPPC_ERR_STATE",
+                              "PPPC_ERR_NEWTON",
+                              "PPPC_ERR_LINEAR",
+                              "PPPC_ERR_BREAKDOWN",
+                              "PPPC_ERR_NAN",
+                              "PPPC_ERR_TIMEOUT",
+                              "PPPC_ERR_NOT_CONVERGED",
+                              "PPPC_ERR_UNSUPPORTED",
+                              "PPPC_ERR_NOMEM"};
+
+pppc_status fail(pppc_handle* h, pppc_status s, const std::string& msg) {
+    h->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? PPPC_ERR_NOMEM : PPPC_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define TRY(expr)                      \
+    do {                               \
+        pppc_status s_ = (expr);       \
+        if (s_ != PPPC_OK) return s_;  \
+    } while (0)
+
+void* dev_alloc(pppc_handle* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* ptr = nullptr;
+    if (h->cfg.alloc) {
+        ptr = h->cfg.alloc(bytes, h->cfg.alloc_ctx);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) h->allocs.push_back(ptr);
+    return ptr;
+}
+
+void free_all(pppc_handle* h) {
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (void* ptr : h->allocs) {
+        if (h->cfg.free_fn)
+            h->cfg.free_fn(ptr, h->cfg.alloc_ctx);
+        else
+            cudaFree(ptr);
+    }
+    h->allocs.clear();
+    h->has_mesh = false;
+}
+
+template <typename T>
+pppc_status alloc_n(pppc_handle* h, T** out, size_t n) {
+    *out = static_cast<T*>(dev_alloc(h, n * sizeof(T)));
+    if (!*out) return fail(h, PPPC_ERR_NOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    return PPPC_OK;
+}
+
+template <typename T>
+pppc_status upload(pppc_handle* h, T** out, const std::vector<T>& v) {
+    TRY(alloc_n(h, out, v.size()));
+    if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->st));
+    return PPPC_OK;
+}
+
+pppc_status device_status(pppc_handle* h, const char* where) {
+    CK(cudaStreamSynchronize(h->st));
+    int code = 0;
+    CK(cudaMemcpy(&code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code == 0) return PPPC_OK;
+    std::string w(where);
+    switch (code) {
+        case DEV_ERR_NEWTON: return fail(h, PPPC_ERR_NEWTON, w + ": Newton iteration cap reached");
+        case DEV_ERR_LINEAR: return fail(h, PPPC_ERR_LINEAR, w + ": linear-solver iteration cap reached");
+        case DEV_ERR_BREAKDOWN: return fail(h, PPPC_ERR_BREAKDOWN, w + ": Krylov breakdown");
+        case DEV_ERR_NAN: return fail(h, PPPC_ERR_NAN, w + ": non-finite residual");
+        case DEV_ERR_TIMEOUT: return fail(h, PPPC_ERR_TIMEOUT, w + ": grid barrier timed out");
+        case DEV_ERR_GEOMETRY: return fail(h, PPPC_ERR_INVALID_ARG, w + ": zero-area or non-finite triangle");
+        default: return fail(h, PPPC_ERR_CUDA, w + ": unknown device status " + std::to_string(code));
+    }
+}
+
+pppc_status reset_control(pppc_handle* h) {
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->st));
+    return PPPC_OK;
+}
+
+pppc_status need_ready(pppc_handle* h) {
+    if (!h) return PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    if (!h->has_source) return fail(h, PPPC_ERR_STATE, "pppc_set_source has not been called");
+    return PPPC_OK;
+}
+
+// ---- stages of one iteration ----------------------------------------------
+
+// F = fine sweep of the lanes in Uin (F may not alias Uin).
+pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
+    const size_t lane_bytes = (size_t)h->hm.ndof * h->NB * sizeof(double);
+    CK(cudaMemcpyAsync(Fout, Uin, lane_bytes, cudaMemcpyDeviceToDevice, h->st));
+    TRY(reset_control(h));
+    FineArgs a{};
+    a.mesh = h->md;
+    a.src = h->src;
+    a.N = h->N;
+    a.NB = h->NB;
+    a.n_fine = h->cfg.n_fine;
+    a.dt = h->dt;
+    a.inv_dt = 1.0 / h->dt;
+    a.tol_abs = h->cfg.tol_newton * h->gnorm * [&] {
+        double s = 0.0;
+        for (int j = 0; j < h->src.n_harm; ++j) s += std::fabs(h->src.amp[j]);
+        return s;
+    }();
+    a.tol_lin = h->fp32 ? std::max(h->cfg.tol_lin, kFp32KrylovFloor) : h->cfg.tol_lin;
+    a.max_newton = h->cfg.max_newton;
+    a.max_lin = h->cfg.max_lin;
+    a.u = Fout;
+    a.uprev = h->uprev;
+    a.elem = h->elem;
+    a.r = h->r;
+    a.z = h->z;
+    a.w = h->w;
+    a.p = h->p;
+    a.s = h->s;
+    a.J = h->J;
+    a.invd_sp = h->invd;
+    a.part = h->part;
+    a.sums = h->sums;
+    a.bar = h->bar;
+    a.status = h->status;
+    a.counters = h->counters;
+    if (h->trace_cap > 0) {
+        CK(cudaMemsetAsync(h->trace_len, 0, sizeof(int), h->st));
+        a.trace = h->trace;
+        a.trace_cap = h->trace_cap;
+        a.trace_len = h->trace_len;
+    }
+    CK(cudaEventRecord(h->ev[0], h->st));
+    CK(launch_fine_sweep(a, h->fp32, h->fine_cfg, h->st));
+    h->stats.launches += 1;
+    CK(cudaEventRecord(h->ev[1], h->st));
+    TRY(device_status(h, "fine propagators"));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+    h->stats.fine_ms += ms;
+    return PPPC_OK;
+}
+
+// jumps d and ||d||^2, ||F||^2 into h->jsums
+pppc_status run_jumps(pppc_handle* h, const double* Ul, const double* Fl, double* rel_res) {
+    CK(cudaEventRecord(h->ev[2], h->st));
+    launch_jumps(h->hm.ndof, h->N, h->NB, Ul, Fl, h->d, h->part, h->jsums, h->st);
+    h->stats.launches += 2;
+    CK(cudaEventRecord(h->ev[3], h->st));
+    CK(cudaGetLastError());
+    double js[2];
+    CK(cudaMemcpyAsync(js, h->jsums, sizeof js, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const double rr = js[1] > 0.0 ? std::sqrt(js[0] / js[1]) : (js[0] > 0.0 ? INFINITY : 0.0);
+    if (rel_res) *rel_res = rr;
+    h->stats.rel_res = rr;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+    h->stats.coarse_ms += ms;
+    if (!std::isfinite(js[0]) || !std::isfinite(js[1])) return fail(h, PPPC_ERR_NAN, "non-finite jump norm");
+    return PPPC_OK;
+}
+
+// Unew = coarse-corrected state from Ul, Fl and the jumps in h->d.
+pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl, double* Unew) {
+    const int lin = h->cfg.coarse_lin;
+    CK(cudaEventRecord(h->ev[2], h->st));
+    if (lin != PPPC_COARSE_ZERO_FIELD && h->md.n_nl > 0) {
+        launch_elem_data(h->md, h->NB, Ul, h->elem, h->st);
+        h->stats.launches += 1;
+    }
+    if (h->md.n_slots > 0) {
+        launch_kbar(h->md, h->N, h->NB, lin, h->elem, h->Kbar, h->st);
+        h->stats.launches += 1;
+    }
+    if (h->md.n_sp > 0) {
+        launch_coarse_rhs(h->md, h->N, h->NB, h->H, 1.0 / h->dT, h->d, h->tw, h->y, h->b, h->st);
+        h->stats.launches += 2;
+    }
+    CK(cudaGetLastError());
+    TRY(reset_control(h));
+    CocgArgs c{};
+    c.mesh = h->md;
+    c.N = h->N;
+    c.H = h->H;
+    c.inv_dT = 1.0 / h->dT;
+    // FP32 Krylov recurrences cannot resolve FP64-level tolerances; an inexact
+    // coarse solve only slows PP-PC (its fixed point does not depend on it).
+    c.tol = h->coarse_fp32 ? std::max(h->cfg.tol_coarse, kFp32KrylovFloor) : h->cfg.tol_coarse;
+    c.max_it = h->cfg.max_coarse;
+    c.Kbar = h->Kbar;
+    c.tw = h->tw;
+    c.b = h->b;
+    c.x = h->cx;
+    c.r = h->cr;
+    c.z = h->cz;
+    c.w = h->cw;
+    c.p = h->cp;
+    c.s = h->cs;
+    c.invd_sp = h->cinvd;
+    c.part = h->part;
+    c.sums = h->sums;
+    c.bar = h->bar;
+    c.status = h->status;
+    c.counters = h->counters;
+    CK(launch_cocg(c, h->coarse_fp32, h->cocg_cfg, h->st));
+    h->stats.launches += 1;
+    TRY(device_status(h, "harmonic solves"));
+    launch_idft_update(h->hm.ndof, h->N, h->NB, h->H, h->coarse_fp32, h->cx, Fl, h->tw, Unew, h->st);
+    h->stats.launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev[3], h->st));
+    CK(cudaEventSynchronize(h->ev[3]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+    h->stats.coarse_ms += ms;
+    return PPPC_OK;
+}
+
+pppc_status begin_call(pppc_handle* h) {
+    CK(cudaMemsetAsync(h->counters, 0, 3 * sizeof(long long), h->st));
+    h->stats = pppc_stats{};
+    return PPPC_OK;
+}
+
+pppc_status end_call(pppc_handle* h) {
+    long long c[3];
+    CK(cudaMemcpyAsync(c, h->counters, sizeof c, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->stats.newton_iters = c[0];
+    h->stats.pcg_iters = c[1];
+    h->stats.cocg_iters = c[2];
+    return PPPC_OK;
+}
+
+pppc_status stage_in(pppc_handle* h, const double* U, int on_device, double* lanes) {
+    const size_t n = (size_t)h->N * h->hm.n_nodes;
+    const double* src = U;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->ext, U, n * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        src = h->ext;
+    }
+    launch_state_to_lanes(h->hm.ndof, h->hm.n_nodes, h->N, h->NB, h->d_node_of_dof, src, lanes, h->st);
+    h->stats.launches += 1;
+    CK(cudaGetLastError());
+    return PPPC_OK;
+}
+
+pppc_status stage_out(pppc_handle* h, const double* lanes, double* U, int on_device) {
+    const size_t n = (size_t)h->N * h->hm.n_nodes;
+    double* dst = on_device ? U : h->ext;
+    launch_lanes_to_state(h->hm.ndof, h->hm.n_nodes, h->N, h->NB, h->d_dof_of_node, lanes, dst, h->st);
+    h->stats.launches += 1;
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(U, h->ext, n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return PPPC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void pppc_config_default(pppc_config* c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->T = 0.02;
+    c->N = 16;
+    c->n_fine = 20;
+    c->precision = PPPC_FP64;
+    c->coarse_lin = PPPC_COARSE_AVG_JACOBIAN;
+    c->tol_newton = 1e-10;
+    c->max_newton = 30;
+    c->tol_lin = 1e-6;
+    c->max_lin = 20000;
+    c->tol_coarse = 1e-10;
+    c->max_coarse = 20000;
+}
+
+const char* pppc_status_string(pppc_status s) {
+    const int i = (int)s;
+    if (i < 0 || i >= (int)(sizeof kStatusNames / sizeof kStatusNames[0])) return "PPPC_ERR_UNKNOWN";
+    return kStatusNames[i];
+}
+
+const char* pppc_last_error(pppc_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return PPPC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!cfg) {
+        g_create_error = "cfg is NULL";
+        return PPPC_ERR_INVALID_ARG;
+    }
+    const pppc_config& c = *cfg;
+    std::string why;
+    if (!(c.T > 0.0) || !std::isfinite(c.T)) why = "T must be positive";
+    else if (c.N < 2 || c.N > kMaxLanes || (c.N % 2) != 0) why = "N must be even and in [2, 1024]";
+    else if (c.n_fine < 1) why = "n_fine must be >= 1";
+    else if (c.precision != PPPC_FP64 && c.precision != PPPC_MIXED) why = "unknown precision";
+    else if (c.coarse_lin < 0 || c.coarse_lin > 2) why = "unknown coarse_lin";
+    else if (!(c.tol_newton > 0.0) || !(c.tol_lin > 0.0) || !(c.tol_coarse > 0.0)) why = "tolerances must be positive";
+    else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
+    else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
+    if (!why.empty()) {
+        g_create_error = why;
+        return PPPC_ERR_INVALID_ARG;
+    }
+    pppc_handle* h = new pppc_handle();
+    h->cfg = c;
+    h->st = static_cast<cudaStream_t>(c.stream);
+    h->N = c.N;
+    h->NB = c.N;
+    h->H = c.N / 2 + 1;
+    h->dT = c.T / c.N;
+    h->dt = c.T / ((double)c.N * c.n_fine);
+    h->fp32 = c.precision == PPPC_MIXED;
+    *out = h;
+    return PPPC_OK;
+}
+
+void pppc_destroy(pppc_handle* h) {
+    if (!h) return;
+    free_all(h);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+int32_t pppc_ndof(pppc_handle* h) { return (h && h->has_mesh) ? h->hm.ndof : 0; }
+
+pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int32_t n_tri, const int32_t* tri,
+                          const int32_t* region, const uint8_t* dirichlet, int32_t n_regions,
+                          const pppc_material* mat) {
+    if (!h) return PPPC_ERR_INVALID_ARG;
+    if (!xy || !tri || !region || !dirichlet || !mat || n_regions < 1)
+        return fail(h, PPPC_ERR_INVALID_ARG, "null array or n_regions < 1");
+    std::vector<int> kinds(n_regions, 0);
+    std::vector<double> mtab((size_t)n_regions * 8, 0.0);
+    for (int r = 0; r < n_regions; ++r) {
+        const pppc_material& q = mat[r];
+        if (!(q.sigma >= 0.0) || !std::isfinite(q.sigma))
+            return fail(h, PPPC_ERR_INVALID_ARG, "region " + std::to_string(r) + ": sigma must be >= 0");
+        if (q.nu_model == PPPC_NU_LINEAR) {
+            if (!(q.nu > 0.0) || !std::isfinite(q.nu))
+                return fail(h, PPPC_ERR_INVALID_ARG, "region " + std::to_string(r) + ": nu must be > 0");
+        } else if (q.nu_model == PPPC_NU_BRAUER) {
+            if (!(q.k1 > 0.0) || !(q.k2 >= 0.0) || !(q.k3 > 0.0) || !std::isfinite(q.k1) || !std::isfinite(q.k2) ||
+                !std::isfinite(q.k3))
+                return fail(h, PPPC_ERR_INVALID_ARG,
+                            "region " + std::to_string(r) + ": Brauer needs k1 > 0, k2 >= 0, k3 > 0");
+            kinds[r] |= ELEM_NONLINEAR;
+        } else {
+            return fail(h, PPPC_ERR_INVALID_ARG, "region " + std::to_string(r) + ": unknown nu_model");
+        }
+        if (q.sigma > 0.0) kinds[r] |= ELEM_CONDUCTIVE;
+        if (q.is_source) kinds[r] |= ELEM_SOURCE;
+        double* m = &mtab[(size_t)r * 8];
+        m[0] = q.sigma;
+        m[1] = (double)q.nu_model;
+        m[2] = q.nu;
+        m[3] = q.k1;
+        m[4] = q.k2;
+        m[5] = q.k3;
+        m[6] = q.is_source ? 1.0 : 0.0;
+    }
+    free_all(h);
+    h->has_source = false;
+    h->trace_cap = 0;
+    for (auto& e : h->ev)
+        if (!e) CK(cudaEventCreate(&e));
+    std::string err;
+    if (!build_host_mesh(n_nodes, n_tri, tri, region, dirichlet, n_regions, kinds.data(), h->hm, err))
+        return fail(h, PPPC_ERR_INVALID_ARG, err);
+    HostMesh& hm = h->hm;
+    bool any_source = false;
+    for (int e = 0; e < n_tri && !any_source; ++e) any_source = (hm.elem_kind[e] & ELEM_SOURCE) != 0;
+    if (!any_source) return fail(h, PPPC_ERR_INVALID_ARG, "no triangle lies in a source region");
+
+    // uploads
+    std::vector<double> vxy(xy, xy + 2 * (size_t)n_nodes);
+    std::vector<int> vtri(tri, tri + 3 * (size_t)n_tri), vreg(region, region + n_tri);
+    double* d_xy;
+    int *d_tri, *d_reg, *d_contrib_ptr, *d_contrib, *d_nl_elems, *d_dcoup_ptr, *d_dcoup;
+    double *d_mat, *d_geom;
+    int *rowptr, *col, *diag_k, *row_slot, *sp_index, *sp_rows, *slot_k, *nl_dofs, *nlc_ptr, *nlc;
+    TRY(upload(h, &d_xy, vxy));
+    TRY(upload(h, &d_tri, vtri));
+    TRY(upload(h, &d_reg, vreg));
+    TRY(upload(h, &d_mat, mtab));
+    TRY(upload(h, &d_contrib_ptr, hm.contrib_ptr));
+    TRY(upload(h, &d_contrib, hm.contrib));
+    TRY(upload(h, &d_nl_elems, hm.nl_elems));
+    TRY(upload(h, &d_dcoup_ptr, hm.dcoup_ptr));
+    TRY(upload(h, &d_dcoup, hm.dcoup));
+    TRY(upload(h, &rowptr, hm.rowptr));
+    TRY(upload(h, &col, hm.col));
+    TRY(upload(h, &diag_k, hm.diag_k));
+    TRY(upload(h, &row_slot, hm.row_slot));
+    TRY(upload(h, &sp_index, hm.sp_index));
+    TRY(upload(h, &sp_rows, hm.sp_rows));
+    TRY(upload(h, &slot_k, hm.slot_k));
+    TRY(upload(h, &nl_dofs, hm.nl_dofs));
+    TRY(upload(h, &nlc_ptr, hm.nlc_ptr));
+    TRY(upload(h, &nlc, hm.nlc));
+    TRY(upload(h, &h->d_node_of_dof, hm.node_of_dof));
+    TRY(upload(h, &h->d_dof_of_node, hm.dof_of_node));
+    TRY(alloc_n(h, &d_geom, (size_t)n_tri * 8));
+    double *Klin, *invdiag_lin, *Mslot, *g, *dlin, *nl_geom, *nl_k, *nlc_ab;
+    float *Klin32, *invdiag_lin32;
+    TRY(alloc_n(h, &Klin, hm.nnz));
+    TRY(alloc_n(h, &Klin32, hm.nnz));
+    TRY(alloc_n(h, &invdiag_lin, hm.ndof));
+    TRY(alloc_n(h, &invdiag_lin32, hm.ndof));
+    TRY(alloc_n(h, &Mslot, hm.n_slots));
+    TRY(alloc_n(h, &g, hm.ndof));
+    TRY(alloc_n(h, &dlin, hm.ndof));
+    TRY(alloc_n(h, &nl_geom, (size_t)hm.n_nl * 8));
+    TRY(alloc_n(h, &nl_k, (size_t)hm.n_nl * 4));
+    TRY(alloc_n(h, &nlc_ab, hm.nlc.size()));
+    TRY(alloc_n(h, &h->tw, 2 * (size_t)h->N));
+    TRY(alloc_n(h, &h->scalars, 2));
+    TRY(alloc_n(h, &h->status, 1));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+
+    SetupArgs sa{};
+    sa.n_tri = n_tri;
+    sa.ndof = hm.ndof;
+    sa.nnz = hm.nnz;
+    sa.n_slots = hm.n_slots;
+    sa.n_nl = hm.n_nl;
+    sa.n_nlc = (int)hm.nlc.size();
+    sa.n_regions = n_regions;
+    sa.N = h->N;
+    sa.xy = d_xy;
+    sa.tri = d_tri;
+    sa.region = d_reg;
+    sa.mat = d_mat;
+    sa.contrib_ptr = d_contrib_ptr;
+    sa.contrib = d_contrib;
+    sa.rowptr = rowptr;
+    sa.diag_k = diag_k;
+    sa.slot_k = slot_k;
+    sa.nl_elems = d_nl_elems;
+    sa.nlc = nlc;
+    sa.dcoup_ptr = d_dcoup_ptr;
+    sa.dcoup = d_dcoup;
+    sa.dlin = dlin;
+    sa.geom = d_geom;
+    sa.Klin = Klin;
+    sa.Klin32 = Klin32;
+    sa.invdiag_lin = invdiag_lin;
+    sa.invdiag_lin32 = invdiag_lin32;
+    sa.Mslot = Mslot;
+    sa.g = g;
+    sa.nl_geom = nl_geom;
+    sa.nl_k = nl_k;
+    sa.nlc_ab = nlc_ab;
+    sa.tw = h->tw;
+    sa.scalars = h->scalars;
+    sa.status = h->status;
+    CK(launch_setup(sa, h->st));
+    TRY(device_status(h, "pppc_set_mesh"));
+    double sc[2];
+    CK(cudaMemcpy(sc, h->scalars, sizeof sc, cudaMemcpyDeviceToHost));
+    h->src_area = sc[0];
+    h->gnorm = sc[1];
+    if (!(h->src_area > 0.0)) return fail(h, PPPC_ERR_INVALID_ARG, "source region has zero area");
+
+    MeshDev& m = h->md;
+    m.ndof = hm.ndof;
+    m.nnz = hm.nnz;
+    m.n_slots = hm.n_slots;
+    m.n_sp = hm.n_sp;
+    m.n_nl = hm.n_nl;
+    m.rowptr = rowptr;
+    m.col = col;
+    m.diag_k = diag_k;
+    m.row_slot = row_slot;
+    m.sp_index = sp_index;
+    m.sp_rows = sp_rows;
+    m.slot_k = slot_k;
+    m.Klin = Klin;
+    m.Klin32 = Klin32;
+    m.invdiag_lin = invdiag_lin;
+    m.invdiag_lin32 = invdiag_lin32;
+    m.Mslot = Mslot;
+    m.g = g;
+    m.dlin = dlin;
+    m.nl_dofs = nl_dofs;
+    m.nl_geom = nl_geom;
+    m.nl_k = nl_k;
+    m.nlc_ptr = nlc_ptr;
+    m.nlc = nlc;
+    m.nlc_ab = nlc_ab;
+
+    // workspace
+    const size_t LV = (size_t)hm.ndof * h->NB;
+    const size_t ts = h->fp32 ? sizeof(float) : sizeof(double);
+    TRY(alloc_n(h, &h->U, LV));
+    TRY(alloc_n(h, &h->Unext, LV));
+    TRY(alloc_n(h, &h->F, LV));
+    TRY(alloc_n(h, &h->uprev, LV));
+    TRY(alloc_n(h, &h->d, LV));
+    TRY(alloc_n(h, &h->elem, (size_t)kElemPlanes * hm.n_nl * h->NB));
+    void** fv[] = {&h->r, &h->z, &h->w, &h->p, &h->s};
+    for (void** v : fv) {
+        *v = dev_alloc(h, LV * ts);
+        if (!*v) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
+        CK(cudaMemsetAsync(*v, 0, LV * ts, h->st));
+    }
+    h->J = dev_alloc(h, (size_t)hm.n_slots * h->NB * ts);
+    h->invd = dev_alloc(h, (size_t)hm.n_sp * h->NB * ts);
+    if (!h->J || !h->invd) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
+    const size_t CV = (size_t)hm.ndof * h->H * 2;
+    const size_t cts = h->coarse_fp32 ? sizeof(float) : sizeof(double);
+    void** cv[] = {&h->cx, &h->cr, &h->cz, &h->cw, &h->cp, &h->cs};
+    for (void** v : cv) {
+        *v = dev_alloc(h, CV * cts);
+        if (!*v) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
+    }
+    h->cinvd = dev_alloc(h, (size_t)hm.n_sp * h->H * 2 * cts);
+    if (!h->cinvd) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
+    TRY(alloc_n(h, &h->y, (size_t)hm.n_sp * h->NB));
+    TRY(alloc_n(h, &h->b, (size_t)hm.n_sp * h->H * 2));
+    TRY(alloc_n(h, &h->Kbar, hm.n_slots));
+    CK(fine_config(h->fp32, h->NB, &h->fine_cfg));
+    CK(cocg_config(h->coarse_fp32, h->H, &h->cocg_cfg));
+    size_t np = std::max((size_t)h->fine_cfg.blocks * 3 * h->NB, (size_t)h->cocg_cfg.blocks * 5 * h->H);
+    np = std::max(np, (size_t)2 * 512);
+    TRY(alloc_n(h, &h->part, np));
+    TRY(alloc_n(h, &h->sums, std::max((size_t)3 * h->NB, (size_t)5 * h->H)));
+    TRY(alloc_n(h, &h->jsums, 2));
+    TRY(alloc_n(h, &h->bar, 1));
+    TRY(alloc_n(h, &h->counters, 3));
+    TRY(alloc_n(h, &h->ext, (size_t)h->N * hm.n_nodes));
+    CK(cudaMemsetAsync(h->U, 0, LV * sizeof(double), h->st));
+    CK(cudaMemsetAsync(h->counters, 0, 3 * sizeof(long long), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->has_mesh = true;
+    return PPPC_OK;
+}
+
+pppc_status pppc_set_source(pppc_handle* h, int32_t n_harm, const double* amp, const double* freq,
+                            const double* phase) {
+    if (!h) return PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    if (n_harm < 1 || n_harm > kMaxHarm || !amp || !freq)
+        return fail(h, PPPC_ERR_INVALID_ARG, "need 1..16 harmonics with amp and freq");
+    SourceDev s{};
+    s.n_harm = n_harm;
+    for (int j = 0; j < n_harm; ++j) {
+        const double cyc = freq[j] * h->cfg.T;
+        if (!std::isfinite(amp[j]) || !std::isfinite(freq[j]) || std::fabs(cyc - std::round(cyc)) > 1e-9 * std::max(1.0, std::fabs(cyc)))
+            return fail(h, PPPC_ERR_INVALID_ARG, "harmonic " + std::to_string(j) + ": freq * T must be an integer");
+        s.amp[j] = amp[j];
+        s.freq[j] = freq[j];
+        s.phase[j] = phase ? phase[j] : 0.0;
+    }
+    h->src = s;
+    h->has_source = true;
+    return PPPC_OK;
+}
+
+pppc_status pppc_set_state(pppc_handle* h, const double* U, int32_t on_device) {
+    if (!h) return PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    if (!U) return fail(h, PPPC_ERR_INVALID_ARG, "U is NULL");
+    TRY(stage_in(h, U, on_device, h->U));
+    CK(cudaStreamSynchronize(h->st));
+    return PPPC_OK;
+}
+
+pppc_status pppc_get_state(pppc_handle* h, double* U, int32_t on_device) {
+    if (!h) return PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    if (!U) return fail(h, PPPC_ERR_INVALID_ARG, "U is NULL");
+    return stage_out(h, h->U, U, on_device);
+}
+
+pppc_status pppc_propagate_fine(pppc_handle* h, const double* U, double* F, int32_t on_device) {
+    TRY(need_ready(h));
+    if (!U || !F) return fail(h, PPPC_ERR_INVALID_ARG, "U or F is NULL");
+    TRY(begin_call(h));
+    TRY(stage_in(h, U, on_device, h->Unext));
+    TRY(run_fine(h, h->Unext, h->F));
+    TRY(end_call(h));
+    h->stats.fine_steps = h->cfg.n_fine;
+    return stage_out(h, h->F, F, on_device);
+}
+
+pppc_status pppc_coarse_update(pppc_handle* h, const double* U, const double* F, double* U_new, double* rel_res,
+                               int32_t on_device) {
+    TRY(need_ready(h));
+    if (!U || !F || !U_new) return fail(h, PPPC_ERR_INVALID_ARG, "U, F or U_new is NULL");
+    TRY(begin_call(h));
+    // lanes: Unext <- U, F <- F (h->U, the handle's state, is untouched)
+    TRY(stage_in(h, U, on_device, h->Unext));
+    TRY(stage_in(h, F, on_device, h->F));
+    TRY(run_jumps(h, h->Unext, h->F, rel_res));
+    TRY(run_coarse_solve(h, h->Unext, h->F, h->uprev));
+    TRY(end_call(h));
+    return stage_out(h, h->uprev, U_new, on_device);
+}
+
+pppc_status pppc_iterate(pppc_handle* h, double* rel_res) {
+    TRY(need_ready(h));
+    TRY(begin_call(h));
+    TRY(run_fine(h, h->U, h->F));
+    TRY(run_jumps(h, h->U, h->F, rel_res));
+    TRY(run_coarse_solve(h, h->U, h->F, h->Unext));
+    CK(cudaStreamSynchronize(h->st));
+    std::swap(h->U, h->Unext);
+    TRY(end_call(h));
+    h->stats.fine_steps = h->cfg.n_fine;
+    h->stats.pppc_iters = 1;
+    return PPPC_OK;
+}
+
+pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_t* iters, double* rel_res) {
+    TRY(need_ready(h));
+    if (!(tol > 0.0) || kmax < 0) return fail(h, PPPC_ERR_INVALID_ARG, "tol must be > 0 and kmax >= 0");
+    TRY(begin_call(h));
+    double rr = INFINITY;
+    for (int k = 0;; ++k) {
+        TRY(run_fine(h, h->U, h->F));
+        TRY(run_jumps(h, h->U, h->F, &rr));
+        h->stats.fine_steps += h->cfg.n_fine;
+        if (rr <= tol || k >= kmax) {
+            if (iters) *iters = k;
+            if (rel_res) *rel_res = rr;
+            h->stats.pppc_iters = k;
+            TRY(end_call(h));
+            h->stats.rel_res = rr;
+            if (rr <= tol) return PPPC_OK;
+            return fail(h, PPPC_ERR_NOT_CONVERGED,
+                        "rel_res " + std::to_string(rr) + " > tol after " + std::to_string(k) + " updates");
+        }
+        TRY(run_coarse_solve(h, h->U, h->F, h->Unext));
+        CK(cudaStreamSynchronize(h->st));
+        std::swap(h->U, h->Unext);
+    }
+}
+
+pppc_status pppc_set_trace(pppc_handle* h, int32_t cap) {
+    if (!h || cap < 0) return h ? fail(h, PPPC_ERR_INVALID_ARG, "cap must be >= 0") : PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    h->trace_cap = 0;
+    if (cap == 0) return PPPC_OK;
+    TRY(alloc_n(h, &h->trace, (size_t)cap * kTraceFields));
+    TRY(alloc_n(h, &h->trace_len, 1));
+    CK(cudaMemsetAsync(h->trace_len, 0, sizeof(int), h->st));
+    h->trace_cap = cap;
+    return PPPC_OK;
+}
+
+pppc_status pppc_get_trace(pppc_handle* h, double* out, int32_t cap, int32_t* n) {
+    if (!h || !out || !n || cap < 0) return h ? fail(h, PPPC_ERR_INVALID_ARG, "null argument") : PPPC_ERR_INVALID_ARG;
+    if (h->trace_cap == 0) return fail(h, PPPC_ERR_STATE, "tracing is off (pppc_set_trace)");
+    int len = 0;
+    CK(cudaMemcpyAsync(&len, h->trace_len, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *n = len;
+    const int k = std::min(std::min(len, cap), h->trace_cap);
+    if (k > 0) CK(cudaMemcpy(out, h->trace, (size_t)k * kTraceFields * sizeof(double), cudaMemcpyDeviceToHost));
+    return PPPC_OK;
+}
+
+pppc_status pppc_get_mesh_counts(pppc_handle* h, pppc_mesh_counts* out) {
+    if (!h || !out) return PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    out->ndof = h->hm.ndof;
+    out->nnz = h->hm.nnz;
+    out->special_rows = h->hm.n_sp;
+    out->special_entries = h->hm.n_slots;
+    out->nonlinear_elems = h->hm.n_nl;
+    return PPPC_OK;
+}
+
+pppc_status pppc_get_stats(pppc_handle* h, pppc_stats* out) {
+    if (!h || !out) return PPPC_ERR_INVALID_ARG;
+    *out = h->stats;
+    return PPPC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// Plain-old-data argument blocks shared by the host driver and the kernels.
+// All device pointers are owned by the handle (api.cu); kernels never free.
+#pragma once
+#include <stdint.h>
+
+namespace pppc {
+
+constexpr int kMaxHarm = 16;        // harmonics of the impressed current
+constexpr int kMaxLanes = 1024;     // N (subintervals) upper bound
+
+// Device status codes (mirrors pppc_status; 0 = ok).
+enum DevStatus : int {
+    DEV_OK = 0,
+    DEV_ERR_NEWTON = 4,
+    DEV_ERR_LINEAR = 5,
+    DEV_ERR_BREAKDOWN = 6,
+    DEV_ERR_NAN = 7,
+    DEV_ERR_TIMEOUT = 8,
+    DEV_ERR_GEOMETRY = 100,   // zero-area or non-finite triangle (set_mesh)
+};
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Sparse structure and constant values of one mesh (Sec. 2, Eq. 1).
+// Rows/columns are free nodes ("dofs").  "Special" rows touch a nonlinear or
+// conductive element; their matrix values differ per lane (fine Jacobian) or
+// per harmonic (coarse systems) and are stored per "slot" = position of an
+// entry among the special rows' entries: slot = row_slot[i] + (k - rowptr[i]).
+struct MeshDev {
+    int ndof, nnz, n_slots, n_sp, n_nl;
+    const int* rowptr;     // [ndof+1]
+    const int* col;        // [nnz]
+    const int* diag_k;     // [ndof] CSR index of the diagonal entry
+    const int* row_slot;   // [ndof] first slot of a special row, -1 otherwise
+    const int* sp_index;   // [ndof] index among special rows, -1 otherwise
+    const int* sp_rows;    // [n_sp] special rows, ascending
+    const int* slot_k;     // [n_slots] CSR index of each slot
+    const double* Klin;    // [nnz] stiffness of the linear-material elements
+    const float* Klin32;   // [nnz] same, FP32 (mixed precision)
+    const double* invdiag_lin;   // [ndof] 1 / Klin(diag) (used on non-special rows)
+    const float* invdiag_lin32;  // [ndof]
+    const double* Mslot;   // [n_slots] conductivity matrix on the special rows
+    const double* g;       // [ndof] source shape (sums to 1)
+    const double* dlin;    // [ndof] K_lin row sums = -(couplings to Dirichlet nodes)
+    // nonlinear (Brauer) elements
+    const int* nl_dofs;    // [n_nl*3] vertex dofs, -1 on the Dirichlet boundary
+    const double* nl_geom; // [n_nl*8] area, gx0, gy0, gx1, gy1, gx2, gy2, pad
+    const double* nl_k;    // [n_nl*4] k1, k2, k3, pad
+    const int* nlc_ptr;    // [n_slots+1] nonlinear contributions of each slot
+    const int* nlc;        // packed e*9 + a*3 + b  (e: nonlinear element index)
+    const double* nlc_ab;  // grad N_a . grad N_b of that element
+};
+
+struct SourceDev {
+    int n_harm;
+    double amp[kMaxHarm];
+    double freq[kMaxHarm];
+    double phase[kMaxHarm];
+};
+
+// Per-lane element data of the nonlinear elements (5 planes of n_nl*NB):
+// c1 = area*nu, c2 = 2*area*dnu/d(B^2), s_a = grad N_a . grad A  (a = 0,1,2)
+constexpr int kElemPlanes = 5;
+
+struct FineArgs {
+    MeshDev mesh;
+    SourceDev src;
+    int N, NB, n_fine;
+    double dt, inv_dt;
+    double tol_abs;          // Newton stop on ||R||_2 per lane
+    double tol_lin;          // PCG relative tolerance floor
+    int max_newton, max_lin;
+    double* u;               // [ndof*NB] Newton state in, F_n out (FP64)
+    double* uprev;           // [ndof*NB]
+    double* elem;            // [5*n_nl*NB]
+    void* r; void* z; void* w; void* p; void* s;   // [ndof*NB] of T
+    void* J;                 // [n_slots*NB] of T
+    void* invd_sp;           // [n_sp*NB] of T
+    double* part;            // [gridDim * 3 * NB]
+    double* sums;            // [3 * NB]
+    GridBarrier* bar;
+    int* status;
+    long long* counters;     // [0] newton iterations, [1] pcg iterations
+    double* trace;           // optional [trace_cap * kTraceFields] Newton records, or null
+    int trace_cap;
+    int* trace_len;          // records written (may exceed trace_cap; extra ones dropped)
+};
+
+// One record per Newton test of the fine sweep:
+// step, Newton iteration, max over lanes of ||R||_2, lanes still iterating,
+// PCG iterations of the solve that preceded this test.
+constexpr int kTraceFields = 5;
+
+struct CocgArgs {
+    MeshDev mesh;
+    int N, H;                // H = N/2 + 1 harmonic lanes
+    double inv_dT;
+    double tol;              // relative tolerance per harmonic
+    int max_it;
+    const double* Kbar;      // [n_slots] coarse stiffness on special rows
+    const double* tw;        // [2*N] exp(-i 2 pi k / N)
+    const double* b;         // [n_sp*H*2] right-hand side (nonzero only on special rows)
+    void* x; void* r; void* z; void* w; void* p; void* s;  // [ndof*H] complex T
+    void* invd_sp;           // [n_sp*H] complex T
+    double* part;            // [gridDim * 5 * H]
+    double* sums;            // [5 * H]
+    GridBarrier* bar;
+    int* status;
+    long long* counters;     // [2] cocg iterations
+};
+
+}  // namespace pppc

@@ -1,0 +1,465 @@
+// Coarse part of one PP-PC iteration (Sec. 2, Eq. 4 with the implicit-Euler
+// coarse step of Eq. 8; the block-cyclic system of Eqs. 9-10 solved by the
+// multi-harmonic method of Sec. 3, Eqs. 11-14).
+//
+// With G linear in its argument (coarse stiffness Kbar frozen within the
+// iteration), subtracting Eq. 9 at U^k from Eq. 9 at U^{k+1} gives, for the
+// update D_n = U_n^{k+1} - U_n^k and the jumps d_n = F_n(U_{n-1}^k) - U_n^k,
+//     Q D_n - C D_{n-1} = Q d_n   (n cyclic),   C = M/dT,  Q = C + Kbar,
+// where the source terms f(T_n) cancel.  The DFT along n (forward sign
+// exp(-i 2 pi p n / N), unnormalised; inverse with 1/N) turns it into one
+// independent shifted system per harmonic p:
+//     (Kbar + (1 - z_p) C) Dhat_p = Q dhat_p,   z_p = exp(-i 2 pi p / N).
+// Writing Dhat_p = dhat_p + W_p,
+//     (Kbar + (1 - z_p) C) W_p = z_p C dhat_p = DFT_p[ C d_{n-1} ],
+// whose right-hand side lives only on rows of the conductive region.  Then
+//     U_n^{k+1} = U_n^k + d_n + w_n = F_n(U_{n-1}^k) + w_n,  w = IDFT(W).
+// For real data only p = 0..N/2 are solved (Hermitian symmetry); each system
+// is complex symmetric and is solved by Jacobi-preconditioned COCG (the
+// conjugate-orthogonal CG), all harmonics in one cooperative launch.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pppc {
+namespace {
+
+inline int grid_for(long long n, int threads, int cap = 65535) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------- jumps --
+constexpr int kJumpBlocks = 512;
+
+__global__ void jumps_kernel(int ndof, int N, int NB, const double* U, const double* F, double* d,
+                             double* part) {
+    __shared__ double red[2][256];
+    double dd = 0.0, ff = 0.0;
+    const long long total = (long long)ndof * NB;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(it % NB);
+        const long long i = it / NB;
+        double v = 0.0;
+        if (n < N) {
+            const double f = F[i * NB + (n + N - 1) % N];
+            v = f - U[it];
+            ff += f * f;
+        }
+        d[it] = v;
+        dd += v * v;
+    }
+    red[0][threadIdx.x] = dd;
+    red[1][threadIdx.x] = ff;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = red[0][0];
+        part[2 * blockIdx.x + 1] = red[1][0];
+    }
+}
+
+__global__ void sum_pairs_kernel(int nblocks, const double* part, double* sums) {
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += part[2 * b + threadIdx.x];
+        sums[threadIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------- coarse linearisation --
+// Kbar on the special rows: K_lin plus the nonlinear stiffness frozen as
+//   lin 0: (1/N) sum_n dK(U)U/dU at U_n   (c1 ab + c2 s_a s_b)
+//   lin 1: (1/N) sum_n K(U_n)             (c1 ab)
+//   lin 2: dK(U)U/dU at U = 0             (|e| (k1 + k3) ab)
+__global__ void kbar_kernel(MeshDev m, int N, int NB, int lin, const double* E, double* Kbar) {
+    const size_t P = (size_t)m.n_nl * NB;
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < m.n_slots; sl += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int c = m.nlc_ptr[sl]; c < m.nlc_ptr[sl + 1]; ++c) {
+            const int pk = m.nlc[c];
+            const int q = pk / 9, ia = (pk / 3) % 3, ib = pk % 3;
+            const double ab = m.nlc_ab[c];
+            if (lin == 2) {
+                v += m.nl_geom[8 * (size_t)q] * (m.nl_k[4 * (size_t)q] + m.nl_k[4 * (size_t)q + 2]) * ab;
+                continue;
+            }
+            double sc = 0.0;
+            for (int n = 0; n < N; ++n) {
+                const size_t o = (size_t)q * NB + n;
+                double t = E[o] * ab;
+                if (lin == 0) t += E[P + o] * E[(2 + ia) * P + o] * E[(2 + ib) * P + o];
+                sc += t;
+            }
+            v += sc / (double)N;
+        }
+        Kbar[sl] = m.Klin[m.slot_k[sl]] + v;
+    }
+}
+
+// ------------------------------------------------ right-hand side + DFT --
+// y = C d on the special rows (all lanes), then b_p = sum_n y_{n-1} z_p^n.
+__global__ void cd_kernel(MeshDev m, int NB, double inv_dT, const double* d, double* y) {
+    const long long total = (long long)m.n_sp * NB;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int sp = (int)(it / NB), n = (int)(it % NB);
+        const int i = m.sp_rows[sp];
+        const int kb = m.rowptr[i], ke = m.rowptr[i + 1], slot0 = m.row_slot[i];
+        double v = 0.0;
+        for (int k = kb; k < ke; ++k) v += m.Mslot[slot0 + (k - kb)] * d[(size_t)m.col[k] * NB + n];
+        y[it] = v * inv_dT;
+    }
+}
+
+__global__ void dft_rhs_kernel(int n_sp, int N, int NB, int H, const double* y, const double* tw,
+                               double* b) {
+    const long long total = (long long)n_sp * H;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int sp = (int)(it / H), p = (int)(it % H);
+        const double* ys = y + (size_t)sp * NB;
+        double re = 0.0, im = 0.0;
+        int k = 0;  // (p * n) mod N
+        for (int n = 0; n < N; ++n) {
+            const double v = ys[(n + N - 1) % N];
+            re += v * tw[2 * k];
+            im += v * tw[2 * k + 1];
+            k += p;
+            if (k >= N) k -= N;
+        }
+        b[2 * it] = re;
+        b[2 * it + 1] = im;
+    }
+}
+
+// ----------------------------------------------------- COCG, all p at once --
+template <typename T> struct cvec;
+template <> struct cvec<double> { using type = double2; };
+template <> struct cvec<float> { using type = float2; };
+
+template <typename T>
+__device__ __forceinline__ cplx ldc(const T* p) {
+    const auto v = *reinterpret_cast<const typename cvec<T>::type*>(p);
+    return {(double)v.x, (double)v.y};
+}
+template <typename T>
+__device__ __forceinline__ cplx ldc_cg(const T* p) {
+    const auto v = __ldcg(reinterpret_cast<const typename cvec<T>::type*>(p));
+    return {(double)v.x, (double)v.y};
+}
+template <typename T>
+__device__ __forceinline__ void stc(T* p, cplx v) {
+    typename cvec<T>::type o;
+    o.x = (T)v.re;
+    o.y = (T)v.im;
+    *reinterpret_cast<typename cvec<T>::type*>(p) = o;
+}
+
+constexpr int CNV = 5;  // per lane: |r|^2, (r,z) re/im, (z,w) re/im
+
+template <typename T>
+__global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
+    extern __shared__ double smem[];
+    const MeshDev m = a.mesh;
+    const int H = a.H;
+    const int tid = threadIdx.x, pl = tid % H, rb = tid / H, RB = blockDim.x / H;
+    double* s_stop = smem;                 // [H]
+    double* s_gold = s_stop + H;           // [2H]
+    double* s_aold = s_gold + 2 * H;       // [2H]
+    double* s_alpha = s_aold + 2 * H;      // [2H]
+    double* s_beta = s_alpha + 2 * H;      // [2H]
+    double* s_red = s_beta + 2 * H;        // [CNV][RB][H]
+    int* s_act = reinterpret_cast<int*>(s_red + CNV * RB * H);
+    __shared__ int s_err;
+
+    T* x = static_cast<T*>(a.x);
+    T* r = static_cast<T*>(a.r);
+    T* z = static_cast<T*>(a.z);
+    T* w = static_cast<T*>(a.w);
+    T* p = static_cast<T*>(a.p);
+    T* s = static_cast<T*>(a.s);
+    T* invd = static_cast<T*>(a.invd_sp);
+    const int rstride = gridDim.x * RB;
+    const int row0 = blockIdx.x * RB + rb;
+    // shift c_p = 1 - z_p of this thread's harmonic
+    const cplx cp = {1.0 - a.tw[2 * pl], -a.tw[2 * pl + 1]};
+    long long iters = 0;
+    if (tid == 0) s_err = 0;
+
+    // init: x = p = s = 0, r = b, z = D^-1 r
+    for (int i = row0; i < m.ndof; i += rstride) {
+        const size_t o = 2 * ((size_t)i * H + pl);
+        const int sp = m.sp_index[i];
+        cplx rv = {0.0, 0.0}, iv;
+        if (sp >= 0) {
+            rv = {a.b[2 * ((size_t)sp * H + pl)], a.b[2 * ((size_t)sp * H + pl) + 1]};
+            const int sl = m.row_slot[i] + (m.diag_k[i] - m.rowptr[i]);
+            const cplx dg = {a.Kbar[sl] + cp.re * m.Mslot[sl] * a.inv_dT, cp.im * m.Mslot[sl] * a.inv_dT};
+            iv = cdiv({1.0, 0.0}, dg);
+            stc<T>(invd + 2 * ((size_t)sp * H + pl), iv);
+        } else {
+            iv = {m.invdiag_lin[i], 0.0};
+        }
+        stc<T>(x + o, {0.0, 0.0});
+        stc<T>(p + o, {0.0, 0.0});
+        stc<T>(s + o, {0.0, 0.0});
+        stc<T>(r + o, rv);
+        stc<T>(z + o, cmul(iv, rv));
+    }
+    if (!grid_sync(a.bar, a.status)) return;
+
+    for (int k = 0;; ++k) {
+        double acc[CNV] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int i = row0; i < m.ndof; i += rstride) {
+            const int kb = m.rowptr[i], ke = m.rowptr[i + 1], slot0 = m.row_slot[i];
+            cplx wv = {0.0, 0.0};
+            if (slot0 < 0) {
+                for (int kk = kb; kk < ke; ++kk) {
+                    const double kv = m.Klin[kk];
+                    const cplx zj = ldc_cg<T>(z + 2 * ((size_t)m.col[kk] * H + pl));
+                    wv.re += kv * zj.re;
+                    wv.im += kv * zj.im;
+                }
+            } else {
+                for (int kk = kb; kk < ke; ++kk) {
+                    const int sl = slot0 + (kk - kb);
+                    const double mv = m.Mslot[sl] * a.inv_dT;
+                    const cplx av = {a.Kbar[sl] + cp.re * mv, cp.im * mv};
+                    wv = cadd(wv, cmul(av, ldc_cg<T>(z + 2 * ((size_t)m.col[kk] * H + pl))));
+                }
+            }
+            const size_t o = 2 * ((size_t)i * H + pl);
+            stc<T>(w + o, wv);
+            const cplx wr = ldc<T>(w + o);   // the stored (rounded) w
+            const cplx ri = ldc<T>(r + o);
+            const cplx zi = ldc<T>(z + o);
+            acc[0] += cabs2(ri);
+            const cplx rz = cmul(ri, zi), zw = cmul(zi, wr);
+            acc[1] += rz.re;
+            acc[2] += rz.im;
+            acc[3] += zw.re;
+            acc[4] += zw.im;
+        }
+#pragma unroll
+        for (int q = 0; q < CNV; ++q) s_red[(q * RB + rb) * H + pl] = acc[q];
+        __syncthreads();
+        for (int o = tid; o < CNV * H; o += blockDim.x) {
+            const int q = o / H, l = o - q * H;
+            double sum = 0.0;
+            for (int t = 0; t < RB; ++t) sum += s_red[(q * RB + t) * H + l];
+            a.part[(size_t)blockIdx.x * CNV * H + o] = sum;
+        }
+        if (!grid_sync_reduce(a.bar, a.status, a.part, a.sums, CNV * H)) return;
+
+        int act = 0;
+        for (int l = tid; l < H; l += blockDim.x) {
+            const double rho = __ldcg(a.sums + l);
+            const cplx gam = {__ldcg(a.sums + H + l), __ldcg(a.sums + 2 * H + l)};
+            const cplx del = {__ldcg(a.sums + 3 * H + l), __ldcg(a.sums + 4 * H + l)};
+            if (k == 0) {
+                s_stop[l] = a.tol * a.tol * rho;
+                s_act[l] = rho > 0.0;
+            }
+            int on = 0;
+            cplx al = {0.0, 0.0}, be = {0.0, 0.0};
+            if (s_act[l]) {
+                if (!isfinite(rho) || !isfinite(gam.re) || !isfinite(gam.im) || !isfinite(del.re) ||
+                    !isfinite(del.im)) {
+                    set_status(a.status, DEV_ERR_NAN);
+                    s_err = 1;
+                } else if (rho <= s_stop[l]) {
+                    s_act[l] = 0;
+                } else if (k >= a.max_it) {
+                    set_status(a.status, DEV_ERR_LINEAR);
+                    s_err = 1;
+                } else {
+                    cplx den = del;
+                    if (k > 0) {
+                        be = cdiv(gam, {s_gold[2 * l], s_gold[2 * l + 1]});
+                        den = csub(del, cdiv(cmul(be, gam), {s_aold[2 * l], s_aold[2 * l + 1]}));
+                    }
+                    if (!(cabs2(den) > 0.0) || !(cabs2(gam) > 0.0)) {
+                        set_status(a.status, DEV_ERR_BREAKDOWN);
+                        s_err = 1;
+                    } else {
+                        al = cdiv(gam, den);
+                        s_gold[2 * l] = gam.re;
+                        s_gold[2 * l + 1] = gam.im;
+                        s_aold[2 * l] = al.re;
+                        s_aold[2 * l + 1] = al.im;
+                        on = 1;
+                    }
+                }
+            }
+            s_alpha[2 * l] = al.re;
+            s_alpha[2 * l + 1] = al.im;
+            s_beta[2 * l] = be.re;
+            s_beta[2 * l + 1] = be.im;
+            act |= on;
+        }
+        const int any = __syncthreads_or(act);
+        if (s_err) return;
+        if (!any) break;
+        ++iters;
+
+        const cplx al = {s_alpha[2 * pl], s_alpha[2 * pl + 1]};
+        const cplx be = {s_beta[2 * pl], s_beta[2 * pl + 1]};
+        for (int i = row0; i < m.ndof; i += rstride) {
+            const size_t o = 2 * ((size_t)i * H + pl);
+            const cplx pv = cadd(ldc<T>(z + o), cmul(be, ldc<T>(p + o)));
+            const cplx sv = cadd(ldc<T>(w + o), cmul(be, ldc<T>(s + o)));
+            const cplx xv = cadd(ldc<T>(x + o), cmul(al, pv));
+            const cplx rv = csub(ldc<T>(r + o), cmul(al, sv));
+            const int sp = m.sp_index[i];
+            const cplx iv = sp >= 0 ? ldc<T>(invd + 2 * ((size_t)sp * H + pl)) : cplx{m.invdiag_lin[i], 0.0};
+            stc<T>(p + o, pv);
+            stc<T>(s + o, sv);
+            stc<T>(x + o, xv);
+            stc<T>(r + o, rv);
+            stc<T>(z + o, cmul(iv, rv));
+        }
+        if (!grid_sync(a.bar, a.status)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) a.counters[2] += iters;
+}
+
+size_t cocg_smem(int H, int threads) {
+    const int RB = threads / H;
+    return (size_t)(9 * H + CNV * RB * H) * sizeof(double) + H * sizeof(int);
+}
+
+// ------------------------------------------------ inverse DFT + update --
+// U_n^{k+1} = F_n(U_{n-1}^k) + (1/N) sum_{p in P} W_p exp(i 2 pi p n / N),
+// the sum taken over the Hermitian spectrum from p = 0..N/2.
+template <typename T>
+__global__ void idft_update_kernel(int ndof, int N, int NB, int H, const T* W, const double* F,
+                                   const double* tw, double* Unew) {
+    const long long total = (long long)ndof * NB;
+    const double invN = 1.0 / (double)N;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(it % NB);
+        const long long i = it / NB;
+        if (n >= N) {
+            Unew[it] = 0.0;
+            continue;
+        }
+        const T* Wi = W + 2 * (size_t)i * H;
+        double acc = (double)Wi[0] + ((n & 1) ? -(double)Wi[2 * (N / 2)] : (double)Wi[2 * (N / 2)]);
+        double mid = 0.0;
+        int k = n;  // (p * n) mod N for p = 1
+        for (int p = 1; p < N / 2; ++p) {
+            mid += (double)Wi[2 * p] * tw[2 * k] + (double)Wi[2 * p + 1] * tw[2 * k + 1];
+            k += n;
+            if (k >= N) k -= N;
+        }
+        acc += 2.0 * mid;
+        Unew[it] = F[i * NB + (n + N - 1) % N] + acc * invN;
+    }
+}
+
+// ------------------------------------------------ layout conversion --
+__global__ void state_to_lanes_kernel(int ndof, int n_nodes, int N, int NB, const int* node_of_dof,
+                                      const double* ext, double* lanes) {
+    const long long total = (long long)ndof * NB;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(it % NB);
+        const long long i = it / NB;
+        lanes[it] = n < N ? ext[(size_t)n * n_nodes + node_of_dof[i]] : 0.0;
+    }
+}
+
+__global__ void lanes_to_state_kernel(int n_nodes, int N, int NB, const int* dof_of_node,
+                                      const double* lanes, double* ext) {
+    const long long total = (long long)n_nodes * N;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int node = (int)(it % n_nodes);
+        const int n = (int)(it / n_nodes);
+        const int d = dof_of_node[node];
+        ext[it] = d >= 0 ? lanes[(size_t)d * NB + n] : 0.0;
+    }
+}
+
+}  // namespace
+
+void launch_jumps(int ndof, int N, int NB, const double* U, const double* F, double* d, double* part,
+                  double* sums, cudaStream_t st) {
+    jumps_kernel<<<kJumpBlocks, 256, 0, st>>>(ndof, N, NB, U, F, d, part);
+    sum_pairs_kernel<<<1, 32, 0, st>>>(kJumpBlocks, part, sums);
+}
+
+void launch_kbar(const MeshDev& m, int N, int NB, int lin, const double* elem, double* Kbar,
+                 cudaStream_t st) {
+    if (m.n_slots == 0) return;
+    kbar_kernel<<<grid_for(m.n_slots, 128), 128, 0, st>>>(m, N, NB, lin, elem, Kbar);
+}
+
+void launch_coarse_rhs(const MeshDev& m, int N, int NB, int H, double inv_dT, const double* d,
+                       const double* tw, double* y, double* b, cudaStream_t st) {
+    if (m.n_sp == 0) return;
+    cd_kernel<<<grid_for((long long)m.n_sp * NB, 256), 256, 0, st>>>(m, NB, inv_dT, d, y);
+    dft_rhs_kernel<<<grid_for((long long)m.n_sp * H, 256), 256, 0, st>>>(m.n_sp, N, NB, H, y, tw, b);
+}
+
+cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg) {
+    if (H < 2 || H > 512) return cudaErrorInvalidValue;
+    const int threads = H * (512 / H);
+    const size_t smem = cocg_smem(H, threads);
+    const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    cfg->blocks = sms * per_sm;
+    cfg->threads = threads;
+    cfg->smem = smem;
+    return cudaSuccess;
+}
+
+cudaError_t launch_cocg(const CocgArgs& a, bool fp32, const LaunchCfg& cfg, cudaStream_t st) {
+    void* args[] = {const_cast<CocgArgs*>(&a)};
+    const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
+    return cudaLaunchCooperativeKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+void launch_idft_update(int ndof, int N, int NB, int H, bool fp32, const void* W, const double* F,
+                        const double* tw, double* Unew, cudaStream_t st) {
+    const int g = grid_for((long long)ndof * NB, 256);
+    if (fp32)
+        idft_update_kernel<float><<<g, 256, 0, st>>>(ndof, N, NB, H, (const float*)W, F, tw, Unew);
+    else
+        idft_update_kernel<double><<<g, 256, 0, st>>>(ndof, N, NB, H, (const double*)W, F, tw, Unew);
+}
+
+void launch_state_to_lanes(int ndof, int n_nodes, int N, int NB, const int* node_of_dof,
+                           const double* ext, double* lanes, cudaStream_t st) {
+    state_to_lanes_kernel<<<grid_for((long long)ndof * NB, 256), 256, 0, st>>>(ndof, n_nodes, N, NB,
+                                                                               node_of_dof, ext, lanes);
+}
+
+void launch_lanes_to_state(int ndof, int n_nodes, int N, int NB, const int* dof_of_node,
+                           const double* lanes, double* ext, cudaStream_t st) {
+    (void)ndof;
+    lanes_to_state_kernel<<<grid_for((long long)n_nodes * N, 256), 256, 0, st>>>(n_nodes, N, NB,
+                                                                                 dof_of_node, lanes, ext);
+}
+
+}  // namespace pppc

@@ -1,0 +1,247 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+Tolerances: relative L2 difference 1e-9 for the FP64 path and 1e-7 for the
+mixed path (FP32 inner PCG/COCG), over the coarse-point states U_n and, for
+the periodic solution, over every fine time level of the period.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle.fem import FEModel
+from oracle.pppc import coarse_update as oracle_coarse_update
+from oracle.pppc import pppc as oracle_pppc
+from oracle.pppc import rel_res as oracle_rel_res
+from oracle.stepping import fine_sweep, one_period, propagate
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOL_MIXED = 1e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_13076_gb300 import _lib
+    from paper_1905_13076_gb300 import build as b
+
+    if not os.path.exists(_lib.LIB_PATH):
+        b.build()
+    return _lib.load()
+
+
+def gpu_solver(prob, **kw):
+    from paper_1905_13076_gb300 import from_problem
+
+    return from_problem(prob, **kw)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def knee_states(prob, seed):
+    """Smooth states with sheath flux densities of 0.3-1.2 T (all nodes, zero
+    on the Dirichlet ring).  Not in equilibrium outside the conductor, so they
+    serve the linear-algebra (coarse) checks, not as initial values."""
+    rng = np.random.default_rng(seed)
+    xy = prob.mesh.xy
+    base = 4e-3 - np.hypot(xy[:, 0], xy[:, 1])
+    a = rng.uniform(0.2, 0.8, size=(prob.N, 1))
+    U = a * base[None] + 1e-7 * rng.standard_normal((prob.N, xy.shape[0]))
+    return U * (prob.mesh.dirichlet == 0)[None]
+
+
+_TRAJ = {}
+
+
+def physical_states(prob, periods=2):
+    """Initial values the fine propagators meet in practice: the coarse-point
+    states of the oracle's sequential time stepping from rest, taken in its
+    second period (consistent with the algebraic equations outside the
+    conductor)."""
+    key = (prob.name, prob.N, prob.n_fine, prob.mesh.nr, prob.mesh.ntheta, periods, bool(prob.nu_model[2] == 0))
+    if key not in _TRAJ:
+        m = FEModel(prob)
+        u = np.zeros(m.ndof)
+        for _ in range(periods):
+            traj = one_period(m, u, prob.N, prob.n_fine, prob.T)
+            u = traj[-1]
+        U = np.zeros((prob.N, prob.mesh.n_nodes))
+        U[:, m.free] = traj[:-1:prob.n_fine]
+        _TRAJ[key] = U
+    return _TRAJ[key].copy()
+
+
+def free(prob, U):
+    return U[:, prob.mesh.dirichlet == 0]
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_fine_sweep_matches_oracle(name):
+    prob = workload(name)
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    with gpu_solver(prob) as s:
+        F = s.propagate_fine(U0)
+        st = s.stats()
+    ref = fine_sweep(m, free(prob, U0), prob.N, prob.n_fine, prob.T)
+    assert rel(free(prob, F), ref) < TOL64
+    for j in range(prob.N):                      # every lane on its own
+        assert rel(free(prob, F)[j], ref[j]) < TOL64
+    assert np.all(F[:, prob.mesh.dirichlet == 1] == 0.0)
+    assert st["newton_iters"] >= prob.n_fine and st["pcg_iters"] > 0
+
+
+def test_fine_sweep_from_rest_is_half_wave_antisymmetric():
+    prob = workload("small")
+    with gpu_solver(prob) as s:
+        F = s.propagate_fine(np.zeros((prob.N, prob.mesh.n_nodes)))
+    h = prob.N // 2
+    assert rel(F[h:], -F[:h]) < 1e-10
+
+
+@pytest.mark.parametrize("lin", ["avg_jacobian", "avg_chord", "zero_field"])
+def test_coarse_update_matches_oracle(lin):
+    prob = workload("small")
+    m = FEModel(prob)
+    rng = np.random.default_rng(3)
+    U = knee_states(prob, 2)
+    F = (U + 1e-5 * rng.standard_normal(U.shape)) * (prob.mesh.dirichlet == 0)[None]
+    with gpu_solver(prob, tol_coarse=1e-13, coarse_lin=lin) as s:
+        Unew, rr = s.coarse_update(U, F)
+    # the oracle's F[j] is F_{j+1}(U_j): the same array
+    ref = oracle_coarse_update(m, free(prob, U), free(prob, F), prob.N, prob.T, coarse="cyclic", lin=lin)
+    assert rel(free(prob, Unew), ref) < TOL64
+    assert rr == pytest.approx(oracle_rel_res(free(prob, U), free(prob, F)), rel=1e-12)
+
+
+def test_pppc_small_matches_oracle():
+    prob = workload("small")
+    m = FEModel(prob)
+    with gpu_solver(prob, tol_coarse=1e-12) as s:
+        iters, rr = s.solve_periodic(tol=1e-11, kmax=40)
+        U = s.get_state()
+        st = s.stats()
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=40)
+    assert ref.converged and rr <= 1e-11
+    assert abs(iters - ref.iterations) <= 1
+    assert rel(free(prob, U), ref.U) < TOL64
+    assert st["pppc_iters"] == iters and st["cocg_iters"] > 0
+
+
+def test_iterates_track_oracle():
+    """The first PP-PC iterates (not only the fixed point) follow the oracle."""
+    prob = workload("small")
+    m = FEModel(prob)
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-30, kmax=3, keep_states=True)
+    with gpu_solver(prob, tol_coarse=1e-13, tol_lin=1e-12) as s:
+        for k in range(3):
+            rr = s.iterate()
+            assert rr == pytest.approx(ref.history[k], rel=1e-7, abs=1e-12)
+            Uk1 = free(prob, s.get_state())
+            Uref = ref.states[k + 1][0] if k + 1 < len(ref.states) else ref.U
+            assert rel(Uk1, Uref) < 1e-8
+
+
+def test_periodic_trajectory_over_the_period():
+    """L2-over-the-period parity: a second GPU decomposition with one fine
+    step per subinterval (N' = N n_fine) has the same fixed point and returns
+    every fine time level; it must match the oracle's periodic trajectory."""
+    prob = workload("small")
+    m = FEModel(prob)
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-12, kmax=40)
+    traj = one_period(m, ref.U[0], prob.N, prob.n_fine, prob.T)[:-1]       # u^0..u^{L-1}
+    L = prob.N * prob.n_fine
+    fine_prob = workload("small", N=L, n_fine=1)
+    with gpu_solver(fine_prob, tol_coarse=1e-12) as s:
+        iters, rr = s.solve_periodic(tol=1e-11, kmax=200)
+        Ug = free(fine_prob, s.get_state())
+    dt = prob.T / L
+    l2 = lambda X: np.sqrt(dt * np.sum(X * X))
+    assert l2(Ug - traj) / l2(traj) < TOL64
+    # and the coarse-point states of the two decompositions agree
+    assert rel(Ug[::prob.n_fine], ref.U) < TOL64
+
+
+def test_mixed_precision_small():
+    prob = workload("small")
+    m = FEModel(prob)
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=40)
+    with gpu_solver(prob, precision="mixed") as s:
+        iters, rr = s.solve_periodic(tol=1e-10, kmax=60)
+        U = s.get_state()
+    assert rel(free(prob, U), ref.U) < TOL_MIXED
+
+
+@pytest.mark.parametrize("over", [dict(N=2), dict(N=20, n_fine=5), dict(n_fine=1), dict(linear_sheath=True)])
+def test_edge_shapes_match_oracle(over):
+    """Smallest N, N not a power of two (the paper's N = 20), one fine step
+    per subinterval, and a mesh without nonlinear elements."""
+    prob = workload("tiny", **over)
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    with gpu_solver(prob, tol_coarse=1e-13) as s:
+        F = s.propagate_fine(U0)
+        iters, rr = s.solve_periodic(tol=1e-11, kmax=80)
+        U = s.get_state()
+    assert rel(free(prob, F), fine_sweep(m, free(prob, U0), prob.N, prob.n_fine, prob.T)) < TOL64
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=80)
+    assert rel(free(prob, U), ref.U) < TOL64
+
+
+def test_medium_sampled_lanes():
+    """Full-size medium mesh (19 801 DOFs, N = 64, 50 fine steps): sampled
+    lanes of one batched fine sweep against the oracle's propagator."""
+    prob = workload("medium")
+    m = FEModel(prob)
+    U0 = np.zeros((prob.N, prob.mesh.n_nodes))          # from rest: lanes differ by their time window
+    with gpu_solver(prob) as s:
+        F = s.propagate_fine(U0)
+    Ff = free(prob, F)
+    U0f = free(prob, U0)
+    for j in (0, 37):
+        ref = propagate(m, j + 1, U0f[j], prob.N, prob.n_fine, prob.T)
+        assert rel(Ff[j], ref) < TOL64
+    h = prob.N // 2
+    assert np.all(np.isfinite(Ff))
+
+
+def test_errors_are_reported():
+    from paper_1905_13076_gb300 import PPPCError
+
+    prob = workload("tiny")
+    with gpu_solver(prob, max_lin=1) as s:
+        with pytest.raises(PPPCError) as e:
+            s.propagate_fine(physical_states(prob))
+        assert e.value.status == 5                      # PPPC_ERR_LINEAR
+    with gpu_solver(prob) as s:
+        it, rr = s.solve_periodic(tol=1e-30, kmax=0, raise_on_fail=False)
+        assert it == 0 and rr == pytest.approx(1.0)     # U = 0: all jumps are F
+        with pytest.raises(PPPCError) as e:
+            s.solve_periodic(tol=1e-30, kmax=1)
+        assert e.value.status == 9                      # PPPC_ERR_NOT_CONVERGED
+    bad = workload("tiny")
+    bad.mesh.tri[0, 0] = bad.mesh.n_nodes + 3
+    with pytest.raises(PPPCError) as e:
+        gpu_solver(bad)
+    assert e.value.status == 1
+
+
+def test_device_pointers_and_stream():
+    torch = pytest.importorskip("torch")
+    prob = workload("tiny")
+    U0 = physical_states(prob)
+    stream = torch.cuda.Stream()
+    with gpu_solver(prob, stream=stream) as s:
+        F_host = s.propagate_fine(U0)
+        with torch.cuda.stream(stream):
+            F_dev = s.propagate_fine(torch.from_numpy(U0).cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(F_dev.cpu().numpy(), F_host)
