@@ -179,6 +179,44 @@ pppc_status pppc_iterate(pppc_handle* h, double* rel_res);
 pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_t* iters,
                                 double* rel_res);
 
+/* ---- Allocation-free harmonic solve ---------------------------------------
+ * The paper has no counterpart to this call.  It exists for callers that
+ * cannot allocate device memory -- for example a plugin that only receives
+ * buffers from a host application which owns every allocation, or a loop
+ * that cannot afford the device synchronisation cudaMalloc implies.  The
+ * handle-based calls above allocate their workspace in pppc_set_mesh, so
+ * such callers cannot use them; this call allocates nothing.
+ *
+ * It solves, for every harmonic p = 0..N/2 at once, the complex symmetric
+ * system (K + (1 - exp(-i 2 pi p / N)) C) x_p = b_p with the same batched
+ * Jacobi-preconditioned COCG kernel as the coarse solve of pppc_iterate.
+ * K and C are real n x n matrices on one CSR pattern (rowptr[n+1], col[nnz],
+ * kval[nnz], cval[nnz]; every row must hold its diagonal entry).  b and x are
+ * complex, interleaved (re, im), laid out [n][N/2+1].  All pointers are
+ * device memory owned by the caller; the call stops when
+ * ||r_p|| <= tol ||b_p|| for every p or after max_it iterations, writes the
+ * iterations done to *iters_out (may be NULL) and synchronises `stream`
+ * (a cudaStream_t, NULL = legacy default stream) before returning.
+ *
+ * Its work vectors live in one static device array of
+ * PPPC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  Limits: N even, 2 <= N <= PPPC_NOALLOC_MAX_N, and
+ * n * (N/2 + 1) <= PPPC_NOALLOC_MAX_UNKNOWNS; larger requests return
+ * PPPC_ERR_INVALID_ARG before any device work, as does a row without a
+ * diagonal entry.  The first call on each device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  Every call shares the array and clears what must start at zero;
+ * calls that overlap on the GPU (other streams or host threads on the same
+ * device) race and must be serialised by the caller.
+ * Errors: INVALID_ARG, LINEAR, BREAKDOWN, NAN, TIMEOUT, CUDA. */
+#define PPPC_NOALLOC_MAX_N 256
+#define PPPC_NOALLOC_MAX_UNKNOWNS 65536
+#define PPPC_NOALLOC_SCRATCH_BYTES (12u << 20)
+pppc_status pppc_harmonic_solve_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col,
+                                        const double* kval, const double* cval, int32_t N,
+                                        const double* b, double* x, double tol, int32_t max_it,
+                                        void* stream, int32_t* iters_out);
+
 /* Iteration counts of the last propagate / coarse / iterate / solve call. */
 pppc_status pppc_get_stats(pppc_handle* h, pppc_stats* out);
 

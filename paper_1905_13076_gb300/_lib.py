@@ -83,6 +83,8 @@ SIGNATURES = {
     "pppc_get_mesh_counts": (c_int32, [c_void_p, POINTER(pppc_mesh_counts)]),
     "pppc_last_error": (c_char_p, [c_void_p]),
     "pppc_status_string": (c_char_p, [c_int32]),
+    "pppc_harmonic_solve_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                              c_void_p, c_void_p, c_double, c_int32, c_void_p, _IPTR]),
 }
 
 _lib = None

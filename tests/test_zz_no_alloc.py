@@ -1,0 +1,116 @@
+"""The allocation-free harmonic solve against the allocating entry point.
+
+pppc_harmonic_solve_noalloc serves callers that cannot allocate device memory
+(its work vectors live in a static device array).  Here it solves the
+harmonic systems of one PP-PC coarse update, and the update rebuilt from its
+solution must equal what pppc_coarse_update (which allocates its workspace in
+pppc_set_mesh) returns for the same U and F, on two calls in a row that share
+the static array.  This file is collected last on purpose.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from oracle.fem import FEModel
+from oracle.pppc import coarse_matrices
+from synth import workload
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_13076_gb300 import _lib
+    from paper_1905_13076_gb300 import build as b
+
+    if not os.path.exists(_lib.LIB_PATH):
+        b.build()
+    return _lib.load()
+
+
+def _states(prob):
+    rng = np.random.default_rng(11)
+    xy = prob.mesh.xy
+    base = 4e-3 - np.hypot(xy[:, 0], xy[:, 1])
+    a = rng.uniform(0.2, 0.8, size=(prob.N, 1))
+    keep = (prob.mesh.dirichlet == 0)[None]
+    U = (a * base[None] + 1e-7 * rng.standard_normal((prob.N, xy.shape[0]))) * keep
+    F = (U + 1e-5 * rng.standard_normal(U.shape)) * keep
+    return U, F
+
+
+def test_noalloc_harmonic_solve_matches_coarse_update(lib):
+    import torch
+
+    from paper_1905_13076_gb300 import from_problem
+
+    prob = workload("small")
+    m = FEModel(prob)
+    N, H = prob.N, prob.N // 2 + 1
+    U, F = _states(prob)
+
+    # the allocating entry point
+    with from_problem(prob, tol_coarse=1e-13) as s:
+        Unew, _ = s.coarse_update(U, F)
+    free = prob.mesh.dirichlet == 0
+    Uf, Ff, Unew_f = U[:, free], F[:, free], Unew[:, free]
+
+    # the same harmonic systems, given as K and C on one CSR pattern
+    _, C, Kbar = coarse_matrices(m, Uf, N, prob.T)
+    S = (abs(Kbar) + abs(C)).tocsr()
+    S.sort_indices()
+    rows = np.repeat(np.arange(S.shape[0]), np.diff(S.indptr))
+    kval = np.asarray(Kbar[rows, S.indices]).ravel()
+    cval = np.asarray(C[rows, S.indices]).ravel()
+    # right-hand sides b_p = sum_n (C d)_{n-1} exp(-i 2 pi p n / N)
+    d = np.roll(Ff, 1, axis=0) - Uf
+    y = (C @ d.T).T
+    b = np.fft.fft(np.roll(y, 1, axis=0), axis=0)[:H]                  # (H, n)
+
+    dev = torch.device("cuda", 0)
+    t_rowptr = torch.from_numpy(S.indptr.astype(np.int32)).to(dev)
+    t_col = torch.from_numpy(S.indices.astype(np.int32)).to(dev)
+    t_k = torch.from_numpy(kval).to(dev)
+    t_c = torch.from_numpy(cval).to(dev)
+    t_b = torch.from_numpy(np.ascontiguousarray(b.T).view(np.float64)).to(dev)   # [n][H] (re, im)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    results = []
+    for call in range(2):
+        t_x = torch.full((S.shape[0], 2 * H), float("nan"), dtype=torch.float64, device=dev)
+        its = ctypes.c_int32()
+        st = lib.pppc_harmonic_solve_noalloc(
+            S.shape[0], t_rowptr.data_ptr(), t_col.data_ptr(), t_k.data_ptr(), t_c.data_ptr(), N,
+            t_b.data_ptr(), t_x.data_ptr(), 1e-13, 20000, stream, ctypes.byref(its))
+        assert st == 0, lib.pppc_status_string(st)
+        assert its.value > 0
+        W = t_x.cpu().numpy().view(np.complex128)                      # (n, H)
+        corr = np.fft.irfft(W.T, n=N, axis=0)                          # inverse DFT over the half spectrum
+        U_rebuilt = np.roll(Ff, 1, axis=0) + corr
+        err = np.linalg.norm(U_rebuilt - Unew_f) / np.linalg.norm(Unew_f)
+        assert err < TOL64, (call, err)
+        results.append(U_rebuilt)
+    assert np.linalg.norm(results[0] - results[1]) <= TOL64 * np.linalg.norm(results[0])
+
+
+def test_noalloc_rejects_oversized_requests(lib):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    dummy = torch.zeros(8, dtype=torch.float64, device=dev)
+    idx = torch.zeros(8, dtype=torch.int32, device=dev)
+    n = 65536 // 9 + 1                                   # n * (N/2 + 1) above the limit for N = 16
+    st = lib.pppc_harmonic_solve_noalloc(n, idx.data_ptr(), idx.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
+                                         16, dummy.data_ptr(), dummy.data_ptr(), 1e-10, 100, None, None)
+    assert st == 1                                       # PPPC_ERR_INVALID_ARG, before any device work
+    st = lib.pppc_harmonic_solve_noalloc(4, idx.data_ptr(), idx.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
+                                         512, dummy.data_ptr(), dummy.data_ptr(), 1e-10, 100, None, None)
+    assert st == 1                                       # N above PPPC_NOALLOC_MAX_N
