@@ -91,7 +91,7 @@ typedef struct pppc_config {
     int32_t coarse_lin;   /* pppc_coarse_lin */
     double tol_newton;    /* fine Newton stop: ||R||_2 <= tol_newton * ||g||_2 * sum_j |amp_j| */
     int32_t max_newton;   /* Newton iteration cap per fine step */
-    double tol_lin;       /* PCG: ||r|| <= max(tol_lin, 0.1 * Newton stop / ||R||) * ||R|| */
+    double tol_lin;       /* smallest PCG forcing term (relative residual of one solve) */
     int32_t max_lin;      /* PCG iteration cap per Newton iteration */
     double tol_coarse;    /* COCG: ||r_p|| <= tol_coarse * ||b_p|| per harmonic */
     int32_t max_coarse;   /* COCG iteration cap */
@@ -99,6 +99,9 @@ typedef struct pppc_config {
     pppc_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc) */
     pppc_free_fn free_fn; /* matching free (NULL: cudaFree) */
     void* alloc_ctx;      /* passed to alloc/free_fn */
+    double eta0;          /* PCG forcing term of each step's first Newton iteration; later ones
+                             follow Eisenstat-Walker, 0.9 (|R_k|/|R_k-1|)^2, within [tol_lin, 0.1] */
+    int32_t predictor;    /* 1: start each fine step's Newton from 2 u^m - u^{m-1} (default 1) */
 } pppc_config;
 
 /* Iteration counts of the most recent iterate / solve / propagate call. */
@@ -116,7 +119,9 @@ typedef struct pppc_stats {
 
 /* Fill *cfg with defaults: T=0.02, N=16, n_fine=20, FP64, averaged Jacobian,
  * tol_newton=1e-10, max_newton=30, tol_lin=1e-6, max_lin=20000,
- * tol_coarse=1e-10, max_coarse=20000, default stream, cudaMalloc. */
+ * tol_coarse=1e-10, max_coarse=20000, default stream, cudaMalloc,
+ * eta0=1e-2, predictor=1.  In PPPC_MIXED the PCG forcing term is at least
+ * 1e-4 (an FP32 solve cannot refine further; Newton's FP64 residual does). */
 void pppc_config_default(pppc_config* cfg);
 
 /* Create a handle for the time grid of Sec. 2: N subintervals of length

@@ -35,7 +35,7 @@ class pppc_config(ctypes.Structure):
         ("coarse_lin", c_int32), ("tol_newton", c_double), ("max_newton", c_int32),
         ("tol_lin", c_double), ("max_lin", c_int32), ("tol_coarse", c_double),
         ("max_coarse", c_int32), ("stream", c_void_p), ("alloc", c_void_p),
-        ("free_fn", c_void_p), ("alloc_ctx", c_void_p),
+        ("free_fn", c_void_p), ("alloc_ctx", c_void_p), ("eta0", c_double), ("predictor", c_int32),
     ]
 
 

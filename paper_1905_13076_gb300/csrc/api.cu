@@ -20,8 +20,10 @@ using namespace pppc;
 
 namespace {
 thread_local std::string g_create_error;
-// Smallest relative residual asked of an FP32 PCG/COCG solve (mixed precision).
-constexpr double kFp32KrylovFloor = 1e-6;
+// Smallest relative residual asked of an FP32 PCG/COCG solve (mixed precision):
+// with the Jacobian rounded to FP32 a solve cannot contract the FP64 Newton
+// residual by much more than ~1e-3, so tighter solves only burn iterations.
+constexpr double kFp32KrylovFloor = 1e-4;
 }
 
 struct pppc_handle {
@@ -40,12 +42,13 @@ struct pppc_handle {
     // lane vectors [ndof][NB]
     double *U = nullptr, *Unext = nullptr, *F = nullptr, *uprev = nullptr, *d = nullptr;
     double* elem = nullptr;
-    void *r = nullptr, *z = nullptr, *w = nullptr, *p = nullptr, *s = nullptr, *J = nullptr, *invd = nullptr;
+    void *r = nullptr, *z = nullptr, *w = nullptr, *p = nullptr, *s = nullptr, *x = nullptr, *J = nullptr,
+         *invd = nullptr;
     // coarse
     double *y = nullptr, *b = nullptr, *Kbar = nullptr, *tw = nullptr;
     void *cx = nullptr, *cr = nullptr, *cz = nullptr, *cw = nullptr, *cp = nullptr, *cs = nullptr, *cinvd = nullptr;
     // reductions and control
-    double *part = nullptr, *sums = nullptr, *jsums = nullptr, *scalars = nullptr;
+    double *part = nullptr, *jsums = nullptr, *scalars = nullptr;
     GridBarrier* bar = nullptr;
     int* status = nullptr;
     long long* counters = nullptr;
@@ -185,6 +188,9 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
         return s;
     }();
     a.tol_lin = h->fp32 ? std::max(h->cfg.tol_lin, kFp32KrylovFloor) : h->cfg.tol_lin;
+    a.eta0 = std::max(h->cfg.eta0, a.tol_lin);
+    a.predictor = h->cfg.predictor;
+    a.x = h->x;
     a.max_newton = h->cfg.max_newton;
     a.max_lin = h->cfg.max_lin;
     a.u = Fout;
@@ -198,7 +204,6 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
     a.J = h->J;
     a.invd_sp = h->invd;
     a.part = h->part;
-    a.sums = h->sums;
     a.bar = h->bar;
     a.status = h->status;
     a.counters = h->counters;
@@ -277,7 +282,6 @@ pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl,
     c.s = h->cs;
     c.invd_sp = h->cinvd;
     c.part = h->part;
-    c.sums = h->sums;
     c.bar = h->bar;
     c.status = h->status;
     c.counters = h->counters;
@@ -354,6 +358,8 @@ void pppc_config_default(pppc_config* c) {
     c->max_lin = 20000;
     c->tol_coarse = 1e-10;
     c->max_coarse = 20000;
+    c->eta0 = 1e-2;
+    c->predictor = 1;
 }
 
 const char* pppc_status_string(pppc_status s) {
@@ -382,6 +388,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (c.precision != PPPC_FP64 && c.precision != PPPC_MIXED) why = "unknown precision";
     else if (c.coarse_lin < 0 || c.coarse_lin > 2) why = "unknown coarse_lin";
     else if (!(c.tol_newton > 0.0) || !(c.tol_lin > 0.0) || !(c.tol_coarse > 0.0)) why = "tolerances must be positive";
+    else if (!(c.eta0 > 0.0) || !(c.eta0 < 1.0)) why = "eta0 must be in (0, 1)";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
@@ -585,7 +592,7 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     TRY(alloc_n(h, &h->uprev, LV));
     TRY(alloc_n(h, &h->d, LV));
     TRY(alloc_n(h, &h->elem, (size_t)kElemPlanes * hm.n_nl * h->NB));
-    void** fv[] = {&h->r, &h->z, &h->w, &h->p, &h->s};
+    void** fv[] = {&h->r, &h->z, &h->w, &h->p, &h->s, &h->x};
     for (void** v : fv) {
         *v = dev_alloc(h, LV * ts);
         if (!*v) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
@@ -608,10 +615,10 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     TRY(alloc_n(h, &h->Kbar, hm.n_slots));
     CK(fine_config(h->fp32, h->NB, &h->fine_cfg));
     CK(cocg_config(h->coarse_fp32, h->H, &h->cocg_cfg));
-    size_t np = std::max((size_t)h->fine_cfg.blocks * 3 * h->NB, (size_t)h->cocg_cfg.blocks * 5 * h->H);
+    // partial sums: two buffers per reduction (fine: T, COCG: FP64) and the jumps' 2 per block
+    size_t np = std::max((size_t)2 * h->fine_cfg.blocks * 3 * h->NB, (size_t)2 * h->cocg_cfg.blocks * 5 * h->H);
     np = std::max(np, (size_t)2 * 512);
     TRY(alloc_n(h, &h->part, np));
-    TRY(alloc_n(h, &h->sums, std::max((size_t)3 * h->NB, (size_t)5 * h->H)));
     TRY(alloc_n(h, &h->jsums, 2));
     TRY(alloc_n(h, &h->bar, 1));
     TRY(alloc_n(h, &h->counters, 3));

@@ -19,9 +19,12 @@ enum DevStatus : int {
     DEV_ERR_GEOMETRY = 100,   // zero-area or non-finite triangle (set_mesh)
 };
 
+// Grid-barrier words, zeroed before every cooperative launch.
 struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int flip;   // plain barrier: the top bit flips once all blocks have arrived
+    unsigned int count;  // reducing barrier: arrivals so far
+    unsigned int gen;    // reducing barrier: released generations
+    unsigned int pad;
 };
 
 // Sparse structure and constant values of one mesh (Sec. 2, Eq. 1).
@@ -71,16 +74,18 @@ struct FineArgs {
     int N, NB, n_fine;
     double dt, inv_dt;
     double tol_abs;          // Newton stop on ||R||_2 per lane
-    double tol_lin;          // PCG relative tolerance floor
+    double tol_lin;          // smallest PCG forcing term
     int max_newton, max_lin;
     double* u;               // [ndof*NB] Newton state in, F_n out (FP64)
     double* uprev;           // [ndof*NB]
     double* elem;            // [5*n_nl*NB]
     void* r; void* z; void* w; void* p; void* s;   // [ndof*NB] of T
+    void* x;                 // [ndof*NB] of T: the Newton correction being solved for
+    double eta0;             // PCG forcing term of the first Newton iteration of a step
+    int predictor;           // 1: start each step's Newton from 2 u^m - u^{m-1}
     void* J;                 // [n_slots*NB] of T
     void* invd_sp;           // [n_sp*NB] of T
-    double* part;            // [gridDim * 3 * NB]
-    double* sums;            // [3 * NB]
+    void* part;              // [2][gridDim][3 * NB] per-block partial sums of type T
     GridBarrier* bar;
     int* status;
     long long* counters;     // [0] newton iterations, [1] pcg iterations
@@ -105,8 +110,7 @@ struct CocgArgs {
     const double* b;         // [n_sp*H*2] right-hand side (nonzero only on special rows)
     void* x; void* r; void* z; void* w; void* p; void* s;  // [ndof*H] complex T
     void* invd_sp;           // [n_sp*H] complex T
-    double* part;            // [gridDim * 5 * H]
-    double* sums;            // [5 * H]
+    double* part;            // [2][gridDim][5 * H] per-block partial sums
     GridBarrier* bar;
     int* status;
     long long* counters;     // [2] cocg iterations

@@ -19,6 +19,7 @@
 // conjugate-orthogonal CG), all harmonics in one cooperative launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -156,11 +157,6 @@ __device__ __forceinline__ cplx ldc(const T* p) {
     return {(double)v.x, (double)v.y};
 }
 template <typename T>
-__device__ __forceinline__ cplx ldc_cg(const T* p) {
-    const auto v = __ldcg(reinterpret_cast<const typename cvec<T>::type*>(p));
-    return {(double)v.x, (double)v.y};
-}
-template <typename T>
 __device__ __forceinline__ void stc(T* p, cplx v) {
     typename cvec<T>::type o;
     o.x = (T)v.re;
@@ -182,8 +178,12 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
     double* s_alpha = s_aold + 2 * H;      // [2H]
     double* s_beta = s_alpha + 2 * H;      // [2H]
     double* s_red = s_beta + 2 * H;        // [CNV][RB][H]
-    int* s_act = reinterpret_cast<int*>(s_red + CNV * RB * H);
+    double* s_sums = s_red + CNV * RB * H; // [CNV][H], identical in every block
+    double* s_tmp = s_sums + CNV * H;      // [blockDim]
+    int* s_act = reinterpret_cast<int*>(s_tmp + blockDim.x);
     __shared__ int s_err;
+    double* part_buf[2] = {a.part, a.part + (size_t)gridDim.x * CNV * H};
+    int parity = 0;
 
     T* x = static_cast<T*>(a.x);
     T* r = static_cast<T*>(a.r);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
             if (slot0 < 0) {
                 for (int kk = kb; kk < ke; ++kk) {
                     const double kv = m.Klin[kk];
-                    const cplx zj = ldc_cg<T>(z + 2 * ((size_t)m.col[kk] * H + pl));
+                    const cplx zj = ldc<T>(z + 2 * ((size_t)m.col[kk] * H + pl));
                     wv.re += kv * zj.re;
                     wv.im += kv * zj.im;
                 }
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
                     const int sl = slot0 + (kk - kb);
                     const double mv = m.Mslot[sl] * a.inv_dT;
                     const cplx av = {a.Kbar[sl] + cp.re * mv, cp.im * mv};
-                    wv = cadd(wv, cmul(av, ldc_cg<T>(z + 2 * ((size_t)m.col[kk] * H + pl))));
+                    wv = cadd(wv, cmul(av, ldc<T>(z + 2 * ((size_t)m.col[kk] * H + pl))));
                 }
             }
             const size_t o = 2 * ((size_t)i * H + pl);
@@ -256,19 +256,22 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
 #pragma unroll
         for (int q = 0; q < CNV; ++q) s_red[(q * RB + rb) * H + pl] = acc[q];
         __syncthreads();
+        double* out = part_buf[parity] + (size_t)blockIdx.x * CNV * H;
         for (int o = tid; o < CNV * H; o += blockDim.x) {
             const int q = o / H, l = o - q * H;
             double sum = 0.0;
             for (int t = 0; t < RB; ++t) sum += s_red[(q * RB + t) * H + l];
-            a.part[(size_t)blockIdx.x * CNV * H + o] = sum;
+            out[o] = sum;
         }
-        if (!grid_sync_reduce(a.bar, a.status, a.part, a.sums, CNV * H)) return;
+        if (!grid_sync(a.bar, a.status)) return;
+        block_reduce_all<double>(part_buf[parity], CNV * H, s_sums, s_tmp);
+        parity ^= 1;
 
         int act = 0;
         for (int l = tid; l < H; l += blockDim.x) {
-            const double rho = __ldcg(a.sums + l);
-            const cplx gam = {__ldcg(a.sums + H + l), __ldcg(a.sums + 2 * H + l)};
-            const cplx del = {__ldcg(a.sums + 3 * H + l), __ldcg(a.sums + 4 * H + l)};
+            const double rho = s_sums[l];
+            const cplx gam = {s_sums[H + l], s_sums[2 * H + l]};
+            const cplx del = {s_sums[3 * H + l], s_sums[4 * H + l]};
             if (k == 0) {
                 s_stop[l] = a.tol * a.tol * rho;
                 s_act[l] = rho > 0.0;
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
 
 size_t cocg_smem(int H, int threads) {
     const int RB = threads / H;
-    return (size_t)(9 * H + CNV * RB * H) * sizeof(double) + H * sizeof(int);
+    return (size_t)(9 * H + CNV * RB * H + CNV * H + threads) * sizeof(double) + H * sizeof(int);
 }
 
 // ------------------------------------------------ inverse DFT + update --
@@ -428,7 +431,8 @@ cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg) {
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    cfg->blocks = sms * per_sm;
+    // one block per SM: every block reads all blocks' partials in each reduction
+    cfg->blocks = sms;
     cfg->threads = threads;
     cfg->smem = smem;
     return cudaSuccess;

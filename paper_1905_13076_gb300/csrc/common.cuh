@@ -1,5 +1,5 @@
-// Device helpers shared by the kernels: bounded grid barrier with a
-// deterministic cross-block reduction, L2-coherent loads, complex arithmetic.
+// Device helpers shared by the kernels: bounded grid barrier, deterministic
+// cross-block reduction, L2-coherent loads, complex arithmetic.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,6 +32,12 @@ __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldcg2(const double* p) { return __ldcg(reinterpret_cast<const double2*>(p)); }
 __device__ __forceinline__ float2 ldcg2(const float* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
 
+// Loads of another block's rows after a grid barrier.  The barrier's
+// acquire (thread 0) followed by __syncthreads orders them after the other
+// blocks' writes, so they may be served by L1.
+__device__ __forceinline__ double2 gld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ float2 gld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
 template <typename T> struct vec2_t;
 template <> struct vec2_t<double> { using type = double2; };
 template <> struct vec2_t<float> { using type = float2; };
@@ -50,33 +56,46 @@ __device__ __forceinline__ void st2(T* p, T a, T b) {
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
-// Arrive at the barrier and wait for all blocks.  Returns false if the wait
-// timed out here or in another block (the caller then returns).
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Spin until pred() holds; gives up after kBarrierTimeoutNs, setting
+// DEV_ERR_TIMEOUT.  Returns false on timeout.
+template <typename Pred>
+__device__ __forceinline__ bool spin_until(Pred pred, int* status) {
+    unsigned long long t0 = 0;
+    unsigned int spins = 0;
+    while (!pred()) {
+        if ((++spins & 1023u) == 0u) {
+            const unsigned long long t = global_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > kBarrierTimeoutNs) {
+                set_status(status, DEV_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Grid barrier with one atomic per block: block 0 adds 2^31 - (blocks - 1),
+// every other block adds 1, so the counter grows by exactly 2^31 per round
+// and its top bit flips when the last block arrives; each block waits for
+// that flip relative to the value it saw.  Returns false if the wait timed
+// out here or in another block (the caller then returns).
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned int g = ld_volatile_u32(&bar->gen);
+        const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
         __threadfence();
-        unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            unsigned long long t0 = global_ns();
-            unsigned int spins = 0;
-            while (ld_volatile_u32(&bar->gen) == g) {
-                if ((++spins & 255u) == 0u && global_ns() - t0 > kBarrierTimeoutNs) {
-                    set_status(status, DEV_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-            __threadfence();
-        }
+        const unsigned int old = atomicAdd(&bar->flip, add);
+        int ok = spin_until([&] { return ((ld_acquire_u32(&bar->flip) ^ old) & 0x80000000u) != 0u; }, status);
+        __threadfence();
         if (ld_volatile_i32(status) == DEV_ERR_TIMEOUT) ok = 0;
         s_ok = ok;
     }
@@ -84,62 +103,54 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
     return s_ok != 0;
 }
 
-// Barrier whose last arriving block sums the per-block partials
-// part[b * nvals + o] over b = 0..gridDim.x-1 in ascending order (a fixed
-// order, so results are bitwise reproducible) into sums[o] before releasing
-// the others.  Every block must have written its partials before calling.
-__device__ __forceinline__ bool grid_sync_reduce(GridBarrier* bar, int* status, const double* part,
-                                                 double* sums, int nvals) {
-    __shared__ int s_last, s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        unsigned int g = ld_volatile_u32(&bar->gen);
-        __threadfence();
-        unsigned int arrived = atomicAdd(&bar->count, 1u);
-        s_last = (arrived == gridDim.x - 1);
-        if (!s_last) {
-            unsigned long long t0 = global_ns();
-            unsigned int spins = 0;
-            while (ld_volatile_u32(&bar->gen) == g) {
-                if ((++spins & 255u) == 0u && global_ns() - t0 > kBarrierTimeoutNs) {
-                    set_status(status, DEV_ERR_TIMEOUT);
-                    s_ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-            __threadfence();
+// Cross-block reduction without a serial last block.  Every block writes its
+// partial sums block-major, part[b * nvals + o]; after one grid_sync every
+// block reduces all of them itself, in one fixed order, into shared memory.
+// All blocks therefore hold bitwise-identical sums and take identical
+// decisions.  Thread t sums the partials of output t % nvals over the blocks
+// b = t / nvals, t / nvals + chunks, ... (chunks = blockDim / nvals), then the
+// chunk results are added in chunk order (tmp[blockDim] holds them).  The caller alternates between two partial buffers so that
+// writing the next partials never overtakes a slower block still reading.
+template <typename RT>
+__device__ __forceinline__ void block_reduce_all(const RT* part, int nvals, RT* sums, RT* tmp) {
+    const int nb = gridDim.x;
+    const int t = threadIdx.x;
+    if (nvals >= (int)blockDim.x) {  // more values than threads: one thread per value
+        for (int o = t; o < nvals; o += blockDim.x) {
+            RT acc = 0;
+            for (int b = 0; b < nb; ++b) acc += __ldcg(part + (size_t)b * nvals + o);
+            sums[o] = acc;
         }
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        const int nb = gridDim.x;
-        for (int o = threadIdx.x; o < nvals; o += blockDim.x) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int b = 0;
-            for (; b + 4 <= nb; b += 4) {
-                a0 += __ldcg(part + (size_t)(b + 0) * nvals + o);
-                a1 += __ldcg(part + (size_t)(b + 1) * nvals + o);
-                a2 += __ldcg(part + (size_t)(b + 2) * nvals + o);
-                a3 += __ldcg(part + (size_t)(b + 3) * nvals + o);
-            }
-            for (; b < nb; ++b) a0 += __ldcg(part + (size_t)b * nvals + o);
-            sums[o] = (a0 + a1) + (a2 + a3);
-        }
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
+        return;
+    }
+    const int chunks = blockDim.x / nvals;
+    if (t < chunks * nvals) {
+        const int o = t % nvals, c = t / nvals;
+        RT acc = 0;
+        // 16 independent loads in flight per round
+        for (int base = c; base < nb; base += 16 * chunks) {
+            RT v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int b = base + k * chunks;
+                v[k] = b < nb ? __ldcg(part + (size_t)b * nvals + o) : (RT)0;
+            }
+#pragma unroll
+            for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                for (int k = 0; k < w; ++k) v[k] += v[k + w];
+            acc += v[0];
         }
+        tmp[t] = acc;
     }
     __syncthreads();
-    if (threadIdx.x == 0 && ld_volatile_i32(status) == DEV_ERR_TIMEOUT) s_ok = 0;
+    for (int o = t; o < nvals; o += blockDim.x) {
+        RT acc = 0;
+        for (int c = 0; c < chunks; ++c) acc += tmp[c * nvals + o];
+        sums[o] = acc;
+    }
     __syncthreads();
-    return s_ok != 0;
 }
 
 // ---- complex helpers (value type double2 / float2 as re, im) -------------

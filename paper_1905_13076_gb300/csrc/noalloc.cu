@@ -114,8 +114,7 @@ extern "C" pppc_status pppc_harmonic_solve_noalloc(int32_t n, const int32_t* row
     void* p = take(vec);
     void* s = take(vec);
     void* invd = take(vec);
-    double* part = static_cast<double*>(take((size_t)cfg.blocks * 5 * H * sizeof(double)));
-    double* sums = static_cast<double*>(take((size_t)5 * H * sizeof(double)));
+    double* part = static_cast<double*>(take(2 * (size_t)cfg.blocks * 5 * H * sizeof(double)));
     GridBarrier* bar = static_cast<GridBarrier*>(take(sizeof(GridBarrier)));
     int* status = static_cast<int*>(take(sizeof(int)));
     long long* counters = static_cast<long long*>(take(3 * sizeof(long long)));
@@ -165,7 +164,6 @@ extern "C" pppc_status pppc_harmonic_solve_noalloc(int32_t n, const int32_t* row
     a.s = s;
     a.invd_sp = invd;
     a.part = part;
-    a.sums = sums;
     a.bar = bar;
     a.status = status;
     a.counters = counters;
