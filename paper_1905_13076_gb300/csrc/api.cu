@@ -39,6 +39,10 @@ struct pppc_handle {
     MeshDev md{};
     int* d_node_of_dof = nullptr;
     int* d_dof_of_node = nullptr;
+    int* d_row_start = nullptr;     // [fine blocks + 1] rows owned by each block of the fine sweep
+    int* d_long_start = nullptr;    // [fine blocks + 1]
+    int* d_long_rows = nullptr;     // rows with more than 32 nonzeros, by owning block
+    int vec_rows = 0;               // > 0: fine-sweep vectors p, s, x, w kept in shared memory
     // lane vectors [ndof][NB]
     double *U = nullptr, *Unext = nullptr, *F = nullptr, *uprev = nullptr, *d = nullptr;
     double* elem = nullptr;
@@ -204,6 +208,10 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
     a.J = h->J;
     a.invd_sp = h->invd;
     a.part = h->part;
+    a.row_start = h->d_row_start;
+    a.long_start = h->d_long_start;
+    a.long_rows = h->d_long_rows;
+    a.vec_rows = h->vec_rows;
     a.bar = h->bar;
     a.status = h->status;
     a.counters = h->counters;
@@ -399,7 +407,8 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     h->cfg = c;
     h->st = static_cast<cudaStream_t>(c.stream);
     h->N = c.N;
-    h->NB = c.N;
+    // lanes padded to the fine kernel's lane-vector width (4 FP32 / 2 FP64)
+    h->NB = c.precision == PPPC_MIXED ? (c.N + 3) / 4 * 4 : c.N;
     h->H = c.N / 2 + 1;
     h->dT = c.T / c.N;
     h->dt = c.T / ((double)c.N * c.n_fine);
@@ -613,7 +622,43 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     TRY(alloc_n(h, &h->y, (size_t)hm.n_sp * h->NB));
     TRY(alloc_n(h, &h->b, (size_t)hm.n_sp * h->H * 2));
     TRY(alloc_n(h, &h->Kbar, hm.n_slots));
-    CK(fine_config(h->fp32, h->NB, &h->fine_cfg));
+    {
+        // Fine sweep: one block per SM, each owning a contiguous range of rows of
+        // about equal cost (nonzeros; per-lane rows count double; long rows,
+        // multiplied by the whole block, carry a fixed extra cost).
+        int dev = 0, nb = 0, smem_optin = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nb, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        std::vector<double> cum(hm.ndof + 1, 0.0);
+        for (int i = 0; i < hm.ndof; ++i) {
+            const int nz = hm.rowptr[i + 1] - hm.rowptr[i];
+            cum[i + 1] = cum[i] + 2.0 + nz * (hm.row_slot[i] >= 0 ? 2.0 : 1.0) + (nz > 32 ? 400.0 : 0.0);
+        }
+        std::vector<int> rs(nb + 1, hm.ndof);
+        rs[0] = 0;
+        int i = 0, rows_max = 0;
+        for (int b = 1; b < nb; ++b) {
+            const double target = cum[hm.ndof] * b / nb;
+            while (i < hm.ndof && cum[i] < target) ++i;
+            rs[b] = i;
+        }
+        for (int b = 0; b < nb; ++b) rows_max = std::max(rows_max, rs[b + 1] - rs[b]);
+        TRY(upload(h, &h->d_row_start, rs));
+        std::vector<int> ls(nb + 1, 0), lrows;
+        for (int b = 0; b < nb; ++b) {
+            for (int r = rs[b]; r < rs[b + 1]; ++r)
+                if (hm.rowptr[r + 1] - hm.rowptr[r] > 32) lrows.push_back(r);
+            ls[b + 1] = (int)lrows.size();
+        }
+        TRY(upload(h, &h->d_long_start, ls));
+        TRY(upload(h, &h->d_long_rows, lrows));
+        // keep p, s, x, w in shared memory when a block's rows fit
+        const int V = h->fp32 ? 4 : 2, G = h->NB / V, threads = G * (1024 / G);
+        h->vec_rows = fine_smem(h->fp32, h->NB, threads, rows_max) + 1024 <= (size_t)smem_optin ? rows_max : 0;
+        CK(fine_config(h->fp32, h->NB, h->vec_rows, &h->fine_cfg));
+        if (h->fine_cfg.blocks != nb) return fail(h, PPPC_ERR_CUDA, "fine sweep: one block per SM expected");
+    }
     CK(cocg_config(h->coarse_fp32, h->H, &h->cocg_cfg));
     // partial sums: two buffers per reduction (fine: T, COCG: FP64) and the jumps' 2 per block
     size_t np = std::max((size_t)2 * h->fine_cfg.blocks * 3 * h->NB, (size_t)2 * h->cocg_cfg.blocks * 5 * h->H);

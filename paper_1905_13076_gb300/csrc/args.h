@@ -86,6 +86,10 @@ struct FineArgs {
     void* J;                 // [n_slots*NB] of T
     void* invd_sp;           // [n_sp*NB] of T
     void* part;              // [2][gridDim][3 * NB] per-block partial sums of type T
+    const int* row_start;    // [gridDim + 1] first row owned by each block
+    const int* long_start;   // [gridDim + 1] ranges of long_rows per block
+    const int* long_rows;    // rows with more than 32 nonzeros, grouped by owning block
+    int vec_rows;            // > 0: p, s, x, w of each block's rows kept in shared memory
     GridBarrier* bar;
     int* status;
     long long* counters;     // [0] newton iterations, [1] pcg iterations

@@ -21,12 +21,16 @@
 // solve stops at the Eisenstat-Walker forcing term, and each step's Newton
 // iteration may start from the linear extrapolation of the last two steps.
 //
-// Layout: vectors are [ndof][NB] (lane fastest); a thread owns 2 adjacent
-// lanes of fixed rows for the whole launch, so row-local data is only ever
-// touched by its owner; other rows' data is read only after a grid barrier.
+// Layout: vectors are [ndof][NB] (lane fastest, NB = N rounded up to the
+// lane-vector width V: 4 FP32 or 2 FP64 lanes, one 16-byte access).  Each
+// block owns a contiguous range of rows (balanced by nonzeros on the host)
+// and a thread owns V adjacent lanes of fixed rows for the whole launch, so
+// row-local data is only touched by its owner; other rows' data is read only
+// after a grid barrier.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 #include "common.cuh"
@@ -81,22 +85,80 @@ constexpr double kPi = 3.141592653589793;
 // kFloorMult of the tolerance: the residual has reached its rounding floor.
 constexpr double kStagnation = 0.5;
 constexpr double kFloorMult = 100.0;
+// Rows with more nonzeros are multiplied by the whole block (see long_rows).
+constexpr int kLongRow = 32;
 
-// Fixed-order in-block sum over the row slots of each lane, written as this
-// block's partials part[blockIdx.x * NV * NB + v * NB + lane].
-template <typename RT>
-__device__ __forceinline__ void block_partials(RT* s_red, int RB, int NB, int rb, int l0, const RT (&v)[NV][2],
-                                               RT* part) {
+// V adjacent lanes of one row, loaded and stored as one vector access.
+template <typename T, int V>
+struct Lanes {
+    T v[V];
+};
+template <typename T, int V>
+__device__ __forceinline__ Lanes<T, V> ldv(const T* p) {
+    Lanes<T, V> r;
+    if constexpr (sizeof(T) * V == 16 && sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        s_red[(q * RB + rb) * NB + l0] = v[q][0];
-        s_red[(q * RB + rb) * NB + l0 + 1] = v[q][1];
+        for (int h = 0; h < V; h += 2) {
+            const auto q = *reinterpret_cast<const typename vec2_t<T>::type*>(p + h);
+            r.v[h] = q.x;
+            r.v[h + 1] = q.y;
+        }
     }
+    return r;
+}
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* p, const Lanes<T, V>& x) {
+    if constexpr (sizeof(T) * V == 16 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+    } else {
+#pragma unroll
+        for (int h = 0; h < V; h += 2) st2<T>(p + h, x.v[h], x.v[h + 1]);
+    }
+}
+
+// Fixed-order in-block reduction over the row groups of each lane, written as
+// this block's partials part[blockIdx.x * NVP * NB + v * NB + lane].  When a
+// warp holds several row groups (G < 32 threads per row) they are first
+// combined with a fixed shuffle tree; the per-warp results are then summed in
+// warp order by one thread per (value, lane).  s_red must hold
+// NVP * (blockDim/32) * NB values (NVP * blockDim/G in the general case).
+template <typename RT, int V, int NVP>
+__device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0, RT (&v)[NVP][V], RT* part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (G < 32 && (32 % G) == 0) {
+#pragma unroll
+        for (int q = 0; q < NVP; ++q)
+#pragma unroll
+            for (int h = 0; h < V; ++h)
+                for (int off = 16; off >= G; off >>= 1) v[q][h] += __shfl_xor_sync(0xffffffffu, v[q][h], off);
+        if (lane < G)
+#pragma unroll
+            for (int q = 0; q < NVP; ++q)
+#pragma unroll
+                for (int h = 0; h < V; ++h) s_red[(q * nwarps + warp) * NB + l0 + h] = v[q][h];
+        __syncthreads();
+        RT* out = part + (size_t)blockIdx.x * NVP * NB;
+        for (int o = threadIdx.x; o < NVP * NB; o += blockDim.x) {
+            const int q = o / NB, l = o - q * NB;
+            RT acc = 0;
+            for (int t = 0; t < nwarps; ++t) acc += s_red[(q * nwarps + t) * NB + l];
+            out[o] = acc;
+        }
+        return;
+    }
+    // general case: one slot per row group, pairwise tree
+    const int RB = blockDim.x / G, rb = threadIdx.x / G;
+#pragma unroll
+    for (int q = 0; q < NVP; ++q)
+#pragma unroll
+        for (int h = 0; h < V; ++h) s_red[(q * RB + rb) * NB + l0 + h] = v[q][h];
     __syncthreads();
-    // fixed pairwise tree over the row slots: fold the upper half onto the lower
     for (int n = RB; n > 1;) {
         const int half = (n + 1) >> 1, cnt = (n - half) * NB;
-        for (int idx = threadIdx.x; idx < NV * cnt; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < NVP * cnt; idx += blockDim.x) {
             const int q = idx / cnt, rem = idx - q * cnt;
             const int t = rem / NB, l = rem - t * NB;
             s_red[(q * RB + t) * NB + l] += s_red[(q * RB + t + half) * NB + l];
@@ -104,20 +166,124 @@ __device__ __forceinline__ void block_partials(RT* s_red, int RB, int NB, int rb
         __syncthreads();
         n = half;
     }
-    RT* out = part + (size_t)blockIdx.x * NV * NB;
-    for (int o = threadIdx.x; o < NV * NB; o += blockDim.x) {
+    RT* out = part + (size_t)blockIdx.x * NVP * NB;
+    for (int o = threadIdx.x; o < NVP * NB; o += blockDim.x) {
         const int q = o / NB, l = o - q * NB;
         out[o] = s_red[(q * RB) * NB + l];
     }
 }
 
+// Residual R(u) of the implicit-Euler step on this thread's rows and lanes,
+// the per-lane Jacobian values of the special rows, r = -R, z = D^-1 r and
+// x = 0.  Accumulates sum R^2 and (r,z) per lane into accR / accz.  Kept out
+// of line: it runs once per Newton iteration, and its register demand
+// (FP64 state and element data) must not constrain the PCG loops.
+template <typename T, int V>
+__device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, int row0, int re, int RB, int l0,
+                                           const double* s_I, double* accR, T* accz, T* xB, size_t vo) {
+    const int NB = a.NB;
+    const size_t P = (size_t)m.n_nl * NB;
+    const double* u = a.u;
+    const double* uprev = a.uprev;
+    const double* E = a.elem;
+    T* r = static_cast<T*>(a.r);
+    T* z = static_cast<T*>(a.z);
+    T* J = static_cast<T*>(a.J);
+    T* invd = static_cast<T*>(a.invd_sp);
+    const T* invdiag_linT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.invdiag_lin32)
+                                                          : reinterpret_cast<const T*>(m.invdiag_lin);
+    for (int i = row0; i < re; i += RB) {
+                const int kb = m.rowptr[i], ke = m.rowptr[i + 1];
+                const int slot0 = m.row_slot[i];
+                const size_t o = (size_t)i * NB + l0;
+                // K_lin u in difference form: sum_{j != i} K_ij (u_j - u_i) + dlin_i u_i
+                const Lanes<double, V> ui = ldv<double, V>(u + o);
+                const double dl = m.dlin[i];
+                double acc[V];
+#pragma unroll
+                for (int h = 0; h < V; ++h) acc[h] = dl * ui.v[h];
+                Lanes<T, V> iv;
+                if (slot0 < 0) {
+                    for (int k = kb; k < ke; ++k) {
+                        const int j = m.col[k];
+                        if (j == i) continue;
+                        const double kv = m.Klin[k];
+                        const Lanes<double, V> uj = ldv<double, V>(u + (size_t)j * NB + l0);
+#pragma unroll
+                        for (int h = 0; h < V; ++h) acc[h] += kv * (uj.v[h] - ui.v[h]);
+                    }
+                    const T d = invdiag_linT[i];
+#pragma unroll
+                    for (int h = 0; h < V; ++h) iv.v[h] = d;
+                } else {
+                    double dg[V];
+                    for (int k = kb; k < ke; ++k) {
+                        const int sl = slot0 + (k - kb);
+                        const int j = m.col[k];
+                        const double kv = m.Klin[k];
+                        const double mv = m.Mslot[sl] * a.inv_dt;
+                        const Lanes<double, V> uj = ldv<double, V>(u + (size_t)j * NB + l0);
+                        const Lanes<double, V> upj = ldv<double, V>(uprev + (size_t)j * NB + l0);
+                        const double kl = (j == i) ? 0.0 : kv;
+                        double Jv[V];
+#pragma unroll
+                        for (int h = 0; h < V; ++h) {
+                            acc[h] += kl * (uj.v[h] - ui.v[h]) + mv * (uj.v[h] - upj.v[h]);
+                            Jv[h] = kv + mv;
+                        }
+                        for (int c = m.nlc_ptr[sl]; c < m.nlc_ptr[sl + 1]; ++c) {
+                            const int pk = m.nlc[c];
+                            const int q = pk / 9, ia = (pk / 3) % 3, ib = pk % 3;
+                            const double ab = m.nlc_ab[c];
+                            const size_t eo = (size_t)q * NB + l0;
+                            const Lanes<double, V> c1 = ldv<double, V>(E + eo);
+                            const Lanes<double, V> c2 = ldv<double, V>(E + P + eo);
+                            const Lanes<double, V> sa = ldv<double, V>(E + (2 + ia) * P + eo);
+                            const Lanes<double, V> sb = ldv<double, V>(E + (2 + ib) * P + eo);
+#pragma unroll
+                            for (int h = 0; h < V; ++h) {
+                                Jv[h] += c1.v[h] * ab + c2.v[h] * sa.v[h] * sb.v[h];
+                                if (j == i) acc[h] += c1.v[h] * sa.v[h];
+                            }
+                        }
+                        Lanes<T, V> jt;
+#pragma unroll
+                        for (int h = 0; h < V; ++h) jt.v[h] = (T)Jv[h];
+                        stv<T, V>(J + (size_t)sl * NB + l0, jt);
+                        if (j == i)
+#pragma unroll
+                            for (int h = 0; h < V; ++h) dg[h] = Jv[h];
+                    }
+#pragma unroll
+                    for (int h = 0; h < V; ++h) iv.v[h] = (T)(1.0 / dg[h]);
+                    stv<T, V>(invd + (size_t)m.sp_index[i] * NB + l0, iv);
+                }
+                const double gi = m.g[i];
+                Lanes<T, V> rv, zv, zero;
+#pragma unroll
+                for (int h = 0; h < V; ++h) {
+                    const double R = acc[h] - s_I[l0 + h] * gi;
+                    rv.v[h] = (T)(-R);
+                    zv.v[h] = rv.v[h] * iv.v[h];
+                    zero.v[h] = (T)0;
+                    accR[h] += R * R;
+                    accz[h] += rv.v[h] * zv.v[h];
+                }
+                stv<T, V>(r + o, rv);
+                stv<T, V>(z + o, zv);
+                stv<T, V>(xB + (o - vo), zero);
+            }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
+    constexpr int V = sizeof(T) == 4 ? 4 : 2;   // lanes per thread: one 16-byte access
+    using RT = T;                               // reductions run in the PCG precision
     extern __shared__ double smem[];
     const MeshDev m = a.mesh;
-    const int NB = a.NB, G = NB >> 1;
+    const int NB = a.NB, G = NB / V;
     const int tid = threadIdx.x, g = tid % G, rb = tid / G, RB = blockDim.x / G;
-    const int l0 = 2 * g;
+    const int l0 = V * g;
     double* s_I = smem;            // current I(t) of each lane at the new time level
     double* s_stop = s_I + NB;     // PCG stop threshold on (r,r)
     double* s_gold = s_stop + NB;  // previous (r,z)
@@ -126,8 +292,6 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     double* s_beta = s_alpha + NB;
     double* s_rprev = s_beta + NB; // ||R|| at the previous Newton test
     double* s_eta = s_rprev + NB;  // previous forcing term
-    // reductions run in the PCG precision: FP32 sums in the mixed path
-    using RT = T;
     RT* s_red = reinterpret_cast<RT*>(s_eta + NB);   // [NV][RB][NB]
     RT* s_sums = s_red + NV * RB * NB;                // [NV][NB], identical in every block
     RT* s_tmp = s_sums + NV * NB;                     // [blockDim]
@@ -142,7 +306,6 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     T* w = static_cast<T*>(a.w);
     T* p = static_cast<T*>(a.p);
     T* s = static_cast<T*>(a.s);
-    T* x = static_cast<T*>(a.x);
     T* J = static_cast<T*>(a.J);
     T* invd = static_cast<T*>(a.invd_sp);
     const T* KlinT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.Klin32)
@@ -153,8 +316,27 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     double* uprev = a.uprev;
     const double* E = a.elem;
     const size_t P = (size_t)m.n_nl * NB;
-    const int rstride = gridDim.x * RB;
-    const int row0 = blockIdx.x * RB + rb;
+    // this block owns the contiguous rows [rs, re)
+    const int rs = a.row_start[blockIdx.x], re = a.row_start[blockIdx.x + 1];
+    // p, s, x, w are only touched by their owning block: when a.vec_rows > 0
+    // they live in shared memory (indexed from row rs), else in global memory
+    T* pB = p;
+    T* sB = s;
+    T* xB = static_cast<T*>(a.x);
+    T* wB = w;
+    size_t vo = 0;
+    if (a.vec_rows > 0) {
+        T* sv = reinterpret_cast<T*>(
+            (reinterpret_cast<uintptr_t>(s_pcg + NB) + 15) & ~static_cast<uintptr_t>(15));
+        const size_t len = (size_t)a.vec_rows * NB;
+        pB = sv;
+        sB = sv + len;
+        xB = sv + 2 * len;
+        wB = sv + 3 * len;
+        vo = (size_t)rs * NB;
+        for (size_t q = tid; q < 2 * len; q += blockDim.x) sv[q] = (T)0;   // p = s = 0
+    }
+    const int row0 = rs + rb;
     const long long n_elem_items = (long long)m.n_nl * NB;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     long long newton_total = 0, pcg_total = 0, pcg_since = 0;
@@ -174,14 +356,17 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
         // u_prev = u^m on own rows; Newton starts from u^m, or from the linear
         // extrapolation 2 u^m - u^{m-1} once a previous step exists
         const bool extrap = a.predictor && step > 0;
-        for (int i = row0; i < m.ndof; i += rstride) {
+        for (int i = row0; i < re; i += RB) {
             const size_t o = (size_t)i * NB + l0;
-            const double2 um = *reinterpret_cast<const double2*>(u + o);
+            const Lanes<double, V> um = ldv<double, V>(u + o);
             if (extrap) {
-                const double2 uo = *reinterpret_cast<const double2*>(uprev + o);
-                st2<double>(u + o, um.x + (um.x - uo.x), um.y + (um.y - uo.y));
+                const Lanes<double, V> uo = ldv<double, V>(uprev + o);
+                Lanes<double, V> un;
+#pragma unroll
+                for (int h = 0; h < V; ++h) un.v[h] = um.v[h] + (um.v[h] - uo.v[h]);
+                stv<double, V>(u + o, un);
             }
-            st2<double>(uprev + o, um.x, um.y);
+            stv<double, V>(uprev + o, um);
         }
         if (extrap && !grid_sync(a.bar, a.status)) return;
         for (long long it = blockIdx.x * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
@@ -190,81 +375,23 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
 
         for (int nit = 0;; ++nit) {
             // ---- residual R(u), per-lane Jacobian of special rows, r = -R, z = D^-1 r, x = 0
-            double accR0 = 0.0, accR1 = 0.0;
-            T accz0 = 0, accz1 = 0;
-            for (int i = row0; i < m.ndof; i += rstride) {
-                const int kb = m.rowptr[i], ke = m.rowptr[i + 1];
-                const int slot0 = m.row_slot[i];
-                // K_lin u in difference form: sum_{j != i} K_ij (u_j - u_i) + dlin_i u_i
-                const double2 ui = *reinterpret_cast<const double2*>(u + (size_t)i * NB + l0);
-                const double dl = m.dlin[i];
-                double a0 = dl * ui.x, a1 = dl * ui.y;
-                T iv0, iv1;
-                if (slot0 < 0) {
-                    for (int k = kb; k < ke; ++k) {
-                        const int j = m.col[k];
-                        if (j == i) continue;
-                        const double kv = m.Klin[k];
-                        const double2 uj = gld2(u + (size_t)j * NB + l0);
-                        a0 += kv * (uj.x - ui.x);
-                        a1 += kv * (uj.y - ui.y);
-                    }
-                    iv0 = iv1 = invdiag_linT[i];
-                } else {
-                    double d0 = 1.0, d1 = 1.0;
-                    for (int k = kb; k < ke; ++k) {
-                        const int sl = slot0 + (k - kb);
-                        const int j = m.col[k];
-                        const double kv = m.Klin[k];
-                        const double mv = m.Mslot[sl] * a.inv_dt;
-                        const double2 uj = gld2(u + (size_t)j * NB + l0);
-                        const double2 upj = gld2(uprev + (size_t)j * NB + l0);
-                        const double kl = (j == i) ? 0.0 : kv;
-                        a0 += kl * (uj.x - ui.x) + mv * (uj.x - upj.x);
-                        a1 += kl * (uj.y - ui.y) + mv * (uj.y - upj.y);
-                        double J0 = kv + mv, J1 = kv + mv;
-                        for (int c = m.nlc_ptr[sl]; c < m.nlc_ptr[sl + 1]; ++c) {
-                            const int pk = m.nlc[c];
-                            const int q = pk / 9, ia = (pk / 3) % 3, ib = pk % 3;
-                            const double ab = m.nlc_ab[c];
-                            const size_t o = (size_t)q * NB + l0;
-                            const double2 c1 = gld2(E + o);
-                            const double2 c2 = gld2(E + P + o);
-                            const double2 sa = gld2(E + (2 + ia) * P + o);
-                            const double2 sb = gld2(E + (2 + ib) * P + o);
-                            J0 += c1.x * ab + c2.x * sa.x * sb.x;
-                            J1 += c1.y * ab + c2.y * sa.y * sb.y;
-                            if (j == i) {
-                                a0 += c1.x * sa.x;
-                                a1 += c1.y * sa.y;
-                            }
-                        }
-                        st2<T>(J + (size_t)sl * NB + l0, (T)J0, (T)J1);
-                        if (j == i) {
-                            d0 = J0;
-                            d1 = J1;
-                        }
-                    }
-                    iv0 = (T)(1.0 / d0);
-                    iv1 = (T)(1.0 / d1);
-                    st2<T>(invd + (size_t)m.sp_index[i] * NB + l0, iv0, iv1);
-                }
-                const double gi = m.g[i];
-                const double R0 = a0 - s_I[l0] * gi, R1 = a1 - s_I[l0 + 1] * gi;
-                const T r0 = (T)(-R0), r1 = (T)(-R1);
-                const T z0 = r0 * iv0, z1 = r1 * iv1;
-                const size_t o = (size_t)i * NB + l0;
-                st2<T>(r + o, r0, r1);
-                st2<T>(z + o, z0, z1);
-                st2<T>(x + o, (T)0, (T)0);
-                accR0 += R0 * R0;
-                accR1 += R1 * R1;
-                accz0 += r0 * z0;
-                accz1 += r1 * z1;
+            double accR[V];
+            T accz[V];
+#pragma unroll
+            for (int h = 0; h < V; ++h) {
+                accR[h] = 0.0;
+                accz[h] = 0;
             }
+            residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo);
             {
-                const RT v[NV][2] = {{(RT)accR0, (RT)accR1}, {(RT)accz0, (RT)accz1}, {(RT)0, (RT)0}};
-                block_partials<RT>(s_red, RB, NB, rb, l0, v, part_buf[parity]);
+                RT v[NV][V];
+#pragma unroll
+                for (int h = 0; h < V; ++h) {
+                    v[0][h] = (RT)accR[h];
+                    v[1][h] = accz[h];
+                    v[2][h] = (RT)0;
+                }
+                block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity]);
             }
             if (!grid_sync(a.bar, a.status)) return;
             block_reduce_all<RT>(part_buf[parity], NV * NB, s_sums, s_tmp);
@@ -301,6 +428,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                         eta = fmin(fmax(eta, a.tol_lin), 0.1);
                         eta = fmax(eta, fmin(0.1, 0.1 * a.tol_abs / Rn));
                         s_eta[l] = eta;
+                        // PCG stops once ||r||_2 (the Newton residual's norm) has dropped by eta
                         s_stop[l] = eta * eta * rr;
                         s_rprev[l] = Rn;
                         al = 1;
@@ -334,40 +462,103 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
 
             // ---- PCG on J x = -R
             for (int k = 0;; ++k) {
-                T rr0 = 0, rr1 = 0, rz0 = 0, rz1 = 0, zw0 = 0, zw1 = 0;
-                for (int i = row0; i < m.ndof; i += rstride) {
+                T rr[V], rz[V], zw[V];
+#pragma unroll
+                for (int h = 0; h < V; ++h) rr[h] = rz[h] = zw[h] = 0;
+                // rows longer than kLongRow are left to the whole block below
+                for (int i = row0; i < re; i += RB) {
                     const int kb = m.rowptr[i], ke = m.rowptr[i + 1];
+                    if (ke - kb > kLongRow) continue;
                     const int slot0 = m.row_slot[i];
-                    T w0 = 0, w1 = 0;
+                    T wv[V];
+#pragma unroll
+                    for (int h = 0; h < V; ++h) wv[h] = 0;
                     if (slot0 < 0) {
                         for (int kk = kb; kk < ke; ++kk) {
                             const T kv = KlinT[kk];
-                            const auto zj = gld2(z + (size_t)m.col[kk] * NB + l0);
-                            w0 += kv * zj.x;
-                            w1 += kv * zj.y;
+                            const Lanes<T, V> zj = ldv<T, V>(z + (size_t)m.col[kk] * NB + l0);
+#pragma unroll
+                            for (int h = 0; h < V; ++h) wv[h] += kv * zj.v[h];
                         }
                     } else {
                         for (int kk = kb; kk < ke; ++kk) {
-                            const auto jv = ld2<T>(J + (size_t)(slot0 + kk - kb) * NB + l0);
-                            const auto zj = gld2(z + (size_t)m.col[kk] * NB + l0);
-                            w0 += jv.x * zj.x;
-                            w1 += jv.y * zj.y;
+                            const Lanes<T, V> jv = ldv<T, V>(J + (size_t)(slot0 + kk - kb) * NB + l0);
+                            const Lanes<T, V> zj = ldv<T, V>(z + (size_t)m.col[kk] * NB + l0);
+#pragma unroll
+                            for (int h = 0; h < V; ++h) wv[h] += jv.v[h] * zj.v[h];
                         }
                     }
                     const size_t o = (size_t)i * NB + l0;
-                    st2<T>(w + o, w0, w1);
-                    const auto ri = ld2<T>(r + o);
-                    const auto zi = ld2<T>(z + o);
-                    rr0 += ri.x * ri.x;
-                    rr1 += ri.y * ri.y;
-                    rz0 += ri.x * zi.x;
-                    rz1 += ri.y * zi.y;
-                    zw0 += zi.x * w0;
-                    zw1 += zi.y * w1;
+                    Lanes<T, V> wl;
+#pragma unroll
+                    for (int h = 0; h < V; ++h) wl.v[h] = wv[h];
+                    stv<T, V>(wB + (o - vo), wl);
+                    const Lanes<T, V> ri = ldv<T, V>(r + o);
+                    const Lanes<T, V> zi = ldv<T, V>(z + o);
+#pragma unroll
+                    for (int h = 0; h < V; ++h) {
+                        rr[h] += ri.v[h] * ri.v[h];
+                        rz[h] += ri.v[h] * zi.v[h];
+                        zw[h] += zi.v[h] * wv[h];
+                    }
+                }
+                // long rows (e.g. the centre node of a polar mesh): every row group
+                // takes a strided share of the nonzeros, then a fixed-order sum
+                for (int lr = a.long_start[blockIdx.x]; lr < a.long_start[blockIdx.x + 1]; ++lr) {
+                    const int i = a.long_rows[lr];
+                    const int kb = m.rowptr[i], ke = m.rowptr[i + 1], slot0 = m.row_slot[i];
+                    T wp[V];
+#pragma unroll
+                    for (int h = 0; h < V; ++h) wp[h] = 0;
+                    for (int kk = kb + rb; kk < ke; kk += RB) {
+                        const Lanes<T, V> zj = ldv<T, V>(z + (size_t)m.col[kk] * NB + l0);
+                        if (slot0 < 0) {
+                            const T kv = KlinT[kk];
+#pragma unroll
+                            for (int h = 0; h < V; ++h) wp[h] += kv * zj.v[h];
+                        } else {
+                            const Lanes<T, V> jv = ldv<T, V>(J + (size_t)(slot0 + kk - kb) * NB + l0);
+#pragma unroll
+                            for (int h = 0; h < V; ++h) wp[h] += jv.v[h] * zj.v[h];
+                        }
+                    }
+                    // combine the row groups: shuffle within a warp, then warps in order
+                    {
+                        RT vv[1][V];
+#pragma unroll
+                        for (int h = 0; h < V; ++h) vv[0][h] = wp[h];
+                        block_partials<RT, V, 1>(s_red, G, NB, l0, vv, s_tmp - (size_t)blockIdx.x * NB);
+                    }
+                    __syncthreads();
+                    if (rb == 0) {
+                        const size_t o = (size_t)i * NB + l0;
+                        T wv[V];
+#pragma unroll
+                        for (int h = 0; h < V; ++h) wv[h] = s_tmp[l0 + h];
+                        Lanes<T, V> wl;
+#pragma unroll
+                        for (int h = 0; h < V; ++h) wl.v[h] = wv[h];
+                        stv<T, V>(wB + (o - vo), wl);
+                        const Lanes<T, V> ri = ldv<T, V>(r + o);
+                        const Lanes<T, V> zi = ldv<T, V>(z + o);
+#pragma unroll
+                        for (int h = 0; h < V; ++h) {
+                            rr[h] += ri.v[h] * ri.v[h];
+                            rz[h] += ri.v[h] * zi.v[h];
+                            zw[h] += zi.v[h] * wv[h];
+                        }
+                    }
+                    __syncthreads();
                 }
                 {
-                    const RT v[NV][2] = {{rr0, rr1}, {rz0, rz1}, {zw0, zw1}};
-                    block_partials<RT>(s_red, RB, NB, rb, l0, v, part_buf[parity]);
+                    RT v[NV][V];
+#pragma unroll
+                    for (int h = 0; h < V; ++h) {
+                        v[0][h] = rr[h];
+                        v[1][h] = rz[h];
+                        v[2][h] = zw[h];
+                    }
+                    block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity]);
                 }
                 if (!grid_sync(a.bar, a.status)) return;
                 block_reduce_all<RT>(part_buf[parity], NV * NB, s_sums, s_tmp);
@@ -391,16 +582,16 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                             s_err = 1;
                         } else {
                             // scalar recurrences in the PCG precision
-                            const T g = (T)gam, d = (T)del;
-                            const T b = (k == 0) ? (T)0 : g / (T)s_gold[l];
-                            const T den = (k == 0) ? d : d - b * g / (T)s_aold[l];
-                            if (!(den > (T)0) || !(g > (T)0)) {
+                            const T gg = (T)gam, d = (T)del;
+                            const T b = (k == 0) ? (T)0 : gg / (T)s_gold[l];
+                            const T den = (k == 0) ? d : d - b * gg / (T)s_aold[l];
+                            if (!(den > (T)0) || !(gg > (T)0)) {
                                 set_status(a.status, DEV_ERR_BREAKDOWN);
                                 s_err = 1;
                             } else {
-                                al = (double)(g / den);
+                                al = (double)(gg / den);
                                 be = (double)b;
-                                s_gold[l] = (double)g;
+                                s_gold[l] = (double)gg;
                                 s_aold[l] = al;
                                 on = 1;
                             }
@@ -416,42 +607,55 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                 ++pcg_total;
                 ++pcg_since;
 
-                const T al0 = (T)s_alpha[l0], al1 = (T)s_alpha[l0 + 1];
-                const T be0 = (T)s_beta[l0], be1 = (T)s_beta[l0 + 1];
-                for (int i = row0; i < m.ndof; i += rstride) {
+                T alv[V], bev[V];
+#pragma unroll
+                for (int h = 0; h < V; ++h) {
+                    alv[h] = (T)s_alpha[l0 + h];
+                    bev[h] = (T)s_beta[l0 + h];
+                }
+                for (int i = row0; i < re; i += RB) {
                     const size_t o = (size_t)i * NB + l0;
-                    const auto zi = ld2<T>(z + o);
-                    const auto wi = ld2<T>(w + o);
-                    const auto pi = ld2<T>(p + o);
-                    const auto si = ld2<T>(s + o);
-                    const auto ri = ld2<T>(r + o);
-                    const auto xi = ld2<T>(x + o);
-                    const T p0 = zi.x + be0 * pi.x, p1 = zi.y + be1 * pi.y;
-                    const T s0 = wi.x + be0 * si.x, s1 = wi.y + be1 * si.y;
-                    const T r0 = ri.x - al0 * s0, r1 = ri.y - al1 * s1;
-                    T iv0, iv1;
+                    const size_t ov = o - vo;
+                    const Lanes<T, V> zi = ldv<T, V>(z + o);
+                    const Lanes<T, V> wi = ldv<T, V>(wB + ov);
+                    const Lanes<T, V> pi = ldv<T, V>(pB + ov);
+                    const Lanes<T, V> si = ldv<T, V>(sB + ov);
+                    const Lanes<T, V> ri = ldv<T, V>(r + o);
+                    const Lanes<T, V> xi = ldv<T, V>(xB + ov);
+                    Lanes<T, V> ivl;
                     const int sp = m.sp_index[i];
                     if (sp < 0) {
-                        iv0 = iv1 = invdiag_linT[i];
+                        const T d = invdiag_linT[i];
+#pragma unroll
+                        for (int h = 0; h < V; ++h) ivl.v[h] = d;
                     } else {
-                        const auto ivv = ld2<T>(invd + (size_t)sp * NB + l0);
-                        iv0 = ivv.x;
-                        iv1 = ivv.y;
+                        ivl = ldv<T, V>(invd + (size_t)sp * NB + l0);
                     }
-                    st2<T>(p + o, p0, p1);
-                    st2<T>(s + o, s0, s1);
-                    st2<T>(r + o, r0, r1);
-                    st2<T>(z + o, r0 * iv0, r1 * iv1);
-                    st2<T>(x + o, xi.x + al0 * p0, xi.y + al1 * p1);
+                    Lanes<T, V> pn, sn, rn, zn, xn;
+#pragma unroll
+                    for (int h = 0; h < V; ++h) {
+                        pn.v[h] = zi.v[h] + bev[h] * pi.v[h];
+                        sn.v[h] = wi.v[h] + bev[h] * si.v[h];
+                        rn.v[h] = ri.v[h] - alv[h] * sn.v[h];
+                        zn.v[h] = rn.v[h] * ivl.v[h];
+                        xn.v[h] = xi.v[h] + alv[h] * pn.v[h];
+                    }
+                    stv<T, V>(pB + ov, pn);
+                    stv<T, V>(sB + ov, sn);
+                    stv<T, V>(r + o, rn);
+                    stv<T, V>(z + o, zn);
+                    stv<T, V>(xB + ov, xn);
                 }
                 if (!grid_sync(a.bar, a.status)) return;
             }
             // ---- u += x on own rows, then element data at the corrected state
-            for (int i = row0; i < m.ndof; i += rstride) {
+            for (int i = row0; i < re; i += RB) {
                 const size_t o = (size_t)i * NB + l0;
-                const auto xi = ld2<T>(x + o);
-                const double2 ui = *reinterpret_cast<const double2*>(u + o);
-                st2<double>(u + o, ui.x + (double)xi.x, ui.y + (double)xi.y);
+                const Lanes<T, V> xi = ldv<T, V>(xB + (o - vo));
+                Lanes<double, V> ui = ldv<double, V>(u + o);
+#pragma unroll
+                for (int h = 0; h < V; ++h) ui.v[h] += (double)xi.v[h];
+                stv<double, V>(u + o, ui);
             }
             if (!grid_sync(a.bar, a.status)) return;
             for (long long it = blockIdx.x * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
@@ -465,19 +669,24 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     }
 }
 
-size_t fine_smem(bool fp32, int NB, int threads) {
-    const int RB = threads / (NB / 2);
-    const size_t rt = fp32 ? sizeof(float) : sizeof(double);
-    return (size_t)8 * NB * sizeof(double) + (size_t)(NV * RB * NB + NV * NB + threads) * rt + 2 * NB * sizeof(int);
-}
 
 }  // namespace
 
-cudaError_t fine_config(bool fp32, int NB, LaunchCfg* cfg) {
-    const int G = NB / 2;
-    if (G < 1 || G > 512) return cudaErrorInvalidValue;
+size_t fine_smem(bool fp32, int NB, int threads, int vec_rows) {
+    const int V = fp32 ? 4 : 2;
+    const int RB = threads / (NB / V);
+    const size_t rt = fp32 ? sizeof(float) : sizeof(double);
+    size_t b = (size_t)8 * NB * sizeof(double) + (size_t)(NV * RB * NB + NV * NB + threads) * rt + 2 * NB * sizeof(int);
+    if (vec_rows > 0) b += 16 + 4 * (size_t)vec_rows * NB * rt;
+    return b;
+}
+
+cudaError_t fine_config(bool fp32, int NB, int vec_rows, LaunchCfg* cfg) {
+    const int V = fp32 ? 4 : 2;
+    const int G = NB / V;
+    if (G < 1 || G > 512 || NB % V != 0) return cudaErrorInvalidValue;
     const int threads = G * (1024 / G);
-    const size_t smem = fine_smem(fp32, NB, threads);
+    const size_t smem = fine_smem(fp32, NB, threads, vec_rows);
     const void* fn = fp32 ? (const void*)fine_sweep_kernel<float> : (const void*)fine_sweep_kernel<double>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
