@@ -42,7 +42,8 @@ struct pppc_handle {
     int* d_row_start = nullptr;     // [fine blocks + 1] rows owned by each block of the fine sweep
     int* d_long_start = nullptr;    // [fine blocks + 1]
     int* d_long_rows = nullptr;     // rows with more than 32 nonzeros, by owning block
-    int vec_rows = 0;               // > 0: fine-sweep vectors p, s, x, w kept in shared memory
+    int vec_rows = 0;               // > 0: fine-sweep vectors p, s, x kept in shared memory
+    int vec_w = 0;                  // 1: and w
     // lane vectors [ndof][NB]
     double *U = nullptr, *Unext = nullptr, *F = nullptr, *uprev = nullptr, *d = nullptr;
     double* elem = nullptr;
@@ -212,6 +213,7 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
     a.long_start = h->d_long_start;
     a.long_rows = h->d_long_rows;
     a.vec_rows = h->vec_rows;
+    a.vec_w = h->vec_w;
     a.bar = h->bar;
     a.status = h->status;
     a.counters = h->counters;
@@ -655,8 +657,15 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         TRY(upload(h, &h->d_long_rows, lrows));
         // keep p, s, x, w in shared memory when a block's rows fit
         const int V = h->fp32 ? 4 : 2, G = h->NB / V, threads = G * (1024 / G);
-        h->vec_rows = fine_smem(h->fp32, h->NB, threads, rows_max) + 1024 <= (size_t)smem_optin ? rows_max : 0;
-        CK(fine_config(h->fp32, h->NB, h->vec_rows, &h->fine_cfg));
+        h->vec_rows = 0;
+        h->vec_w = 0;
+        if (fine_smem(h->fp32, h->NB, threads, rows_max, 4) + 1024 <= (size_t)smem_optin) {
+            h->vec_rows = rows_max;
+            h->vec_w = 1;
+        } else if (fine_smem(h->fp32, h->NB, threads, rows_max, 3) + 1024 <= (size_t)smem_optin) {
+            h->vec_rows = rows_max;
+        }
+        CK(fine_config(h->fp32, h->NB, h->vec_rows, h->vec_w ? 4 : 3, &h->fine_cfg));
         if (h->fine_cfg.blocks != nb) return fail(h, PPPC_ERR_CUDA, "fine sweep: one block per SM expected");
     }
     CK(cocg_config(h->coarse_fp32, h->H, &h->cocg_cfg));

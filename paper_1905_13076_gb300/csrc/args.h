@@ -89,7 +89,8 @@ struct FineArgs {
     const int* row_start;    // [gridDim + 1] first row owned by each block
     const int* long_start;   // [gridDim + 1] ranges of long_rows per block
     const int* long_rows;    // rows with more than 32 nonzeros, grouped by owning block
-    int vec_rows;            // > 0: p, s, x, w of each block's rows kept in shared memory
+    int vec_rows;            // > 0: p, s, x of each block's rows kept in shared memory
+    int vec_w;               // 1: w as well
     GridBarrier* bar;
     int* status;
     long long* counters;     // [0] newton iterations, [1] pcg iterations

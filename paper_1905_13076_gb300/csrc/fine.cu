@@ -119,6 +119,13 @@ __device__ __forceinline__ void stv(T* p, const Lanes<T, V>& x) {
     }
 }
 
+// Slots of the in-block reduction scratch per value and lane: one per warp
+// when the row groups of a warp can be combined by shuffles, else one per
+// row group.
+__host__ __device__ inline int red_slots(int G, int threads) {
+    return (G < 32 && (32 % G) == 0) || G == 32 ? threads / 32 : threads / G;
+}
+
 // Fixed-order in-block reduction over the row groups of each lane, written as
 // this block's partials part[blockIdx.x * NVP * NB + v * NB + lane].  When a
 // warp holds several row groups (G < 32 threads per row) they are first
@@ -292,8 +299,8 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     double* s_beta = s_alpha + NB;
     double* s_rprev = s_beta + NB; // ||R|| at the previous Newton test
     double* s_eta = s_rprev + NB;  // previous forcing term
-    RT* s_red = reinterpret_cast<RT*>(s_eta + NB);   // [NV][RB][NB]
-    RT* s_sums = s_red + NV * RB * NB;                // [NV][NB], identical in every block
+    RT* s_red = reinterpret_cast<RT*>(s_eta + NB);   // [NV][red_slots(G)][NB]
+    RT* s_sums = s_red + NV * red_slots(G, blockDim.x) * NB;  // [NV][NB], identical in every block
     RT* s_tmp = s_sums + NV * NB;                     // [blockDim]
     int* s_newton = reinterpret_cast<int*>(s_tmp + blockDim.x);
     int* s_pcg = s_newton + NB;
@@ -301,13 +308,14 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     RT* part_buf[2] = {static_cast<RT*>(a.part), static_cast<RT*>(a.part) + (size_t)gridDim.x * NV * NB};
     int parity = 0;
 
-    T* r = static_cast<T*>(a.r);
-    T* z = static_cast<T*>(a.z);
+    // the vectors never alias one another
+    T* __restrict__ r = static_cast<T*>(a.r);
+    T* __restrict__ z = static_cast<T*>(a.z);
     T* w = static_cast<T*>(a.w);
     T* p = static_cast<T*>(a.p);
     T* s = static_cast<T*>(a.s);
-    T* J = static_cast<T*>(a.J);
-    T* invd = static_cast<T*>(a.invd_sp);
+    T* __restrict__ J = static_cast<T*>(a.J);
+    T* __restrict__ invd = static_cast<T*>(a.invd_sp);
     const T* KlinT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.Klin32)
                                                    : reinterpret_cast<const T*>(m.Klin);
     const T* invdiag_linT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.invdiag_lin32)
@@ -320,11 +328,12 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     const int rs = a.row_start[blockIdx.x], re = a.row_start[blockIdx.x + 1];
     // p, s, x, w are only touched by their owning block: when a.vec_rows > 0
     // they live in shared memory (indexed from row rs), else in global memory
-    T* pB = p;
-    T* sB = s;
-    T* xB = static_cast<T*>(a.x);
-    T* wB = w;
-    size_t vo = 0;
+    T* __restrict__ pB = p;
+    T* __restrict__ sB = s;
+    T* __restrict__ xB = static_cast<T*>(a.x);
+    T* __restrict__ wB = w;
+    size_t vo = 0;   // row offset of the shared-memory vectors (0: global vectors)
+    size_t wo = 0;
     if (a.vec_rows > 0) {
         T* sv = reinterpret_cast<T*>(
             (reinterpret_cast<uintptr_t>(s_pcg + NB) + 15) & ~static_cast<uintptr_t>(15));
@@ -332,8 +341,11 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
         pB = sv;
         sB = sv + len;
         xB = sv + 2 * len;
-        wB = sv + 3 * len;
         vo = (size_t)rs * NB;
+        if (a.vec_w) {
+            wB = sv + 3 * len;
+            wo = vo;
+        }
         for (size_t q = tid; q < 2 * len; q += blockDim.x) sv[q] = (T)0;   // p = s = 0
     }
     const int row0 = rs + rb;
@@ -492,7 +504,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                     Lanes<T, V> wl;
 #pragma unroll
                     for (int h = 0; h < V; ++h) wl.v[h] = wv[h];
-                    stv<T, V>(wB + (o - vo), wl);
+                    stv<T, V>(wB + (o - wo), wl);
                     const Lanes<T, V> ri = ldv<T, V>(r + o);
                     const Lanes<T, V> zi = ldv<T, V>(z + o);
 #pragma unroll
@@ -538,7 +550,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                         Lanes<T, V> wl;
 #pragma unroll
                         for (int h = 0; h < V; ++h) wl.v[h] = wv[h];
-                        stv<T, V>(wB + (o - vo), wl);
+                        stv<T, V>(wB + (o - wo), wl);
                         const Lanes<T, V> ri = ldv<T, V>(r + o);
                         const Lanes<T, V> zi = ldv<T, V>(z + o);
 #pragma unroll
@@ -613,11 +625,12 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                     alv[h] = (T)s_alpha[l0 + h];
                     bev[h] = (T)s_beta[l0 + h];
                 }
+#pragma unroll 2
                 for (int i = row0; i < re; i += RB) {
                     const size_t o = (size_t)i * NB + l0;
                     const size_t ov = o - vo;
                     const Lanes<T, V> zi = ldv<T, V>(z + o);
-                    const Lanes<T, V> wi = ldv<T, V>(wB + ov);
+                    const Lanes<T, V> wi = ldv<T, V>(wB + (o - wo));
                     const Lanes<T, V> pi = ldv<T, V>(pB + ov);
                     const Lanes<T, V> si = ldv<T, V>(sB + ov);
                     const Lanes<T, V> ri = ldv<T, V>(r + o);
@@ -672,21 +685,22 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
 
 }  // namespace
 
-size_t fine_smem(bool fp32, int NB, int threads, int vec_rows) {
+size_t fine_smem(bool fp32, int NB, int threads, int vec_rows, int vec_count) {
     const int V = fp32 ? 4 : 2;
-    const int RB = threads / (NB / V);
+    const int slots = red_slots(NB / V, threads);
     const size_t rt = fp32 ? sizeof(float) : sizeof(double);
-    size_t b = (size_t)8 * NB * sizeof(double) + (size_t)(NV * RB * NB + NV * NB + threads) * rt + 2 * NB * sizeof(int);
-    if (vec_rows > 0) b += 16 + 4 * (size_t)vec_rows * NB * rt;
+    size_t b = (size_t)8 * NB * sizeof(double) + (size_t)(NV * slots * NB + NV * NB + threads) * rt +
+               2 * NB * sizeof(int);
+    if (vec_rows > 0) b += 16 + (size_t)vec_count * vec_rows * NB * rt;
     return b;
 }
 
-cudaError_t fine_config(bool fp32, int NB, int vec_rows, LaunchCfg* cfg) {
+cudaError_t fine_config(bool fp32, int NB, int vec_rows, int vec_count, LaunchCfg* cfg) {
     const int V = fp32 ? 4 : 2;
     const int G = NB / V;
     if (G < 1 || G > 512 || NB % V != 0) return cudaErrorInvalidValue;
     const int threads = G * (1024 / G);
-    const size_t smem = fine_smem(fp32, NB, threads, vec_rows);
+    const size_t smem = fine_smem(fp32, NB, threads, vec_rows, vec_count);
     const void* fn = fp32 ? (const void*)fine_sweep_kernel<float> : (const void*)fine_sweep_kernel<double>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

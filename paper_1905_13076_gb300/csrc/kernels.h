@@ -44,9 +44,10 @@ struct LaunchCfg {
     int blocks = 0, threads = 0;
     size_t smem = 0;
 };
-// vec_rows > 0: each block keeps p, s, x, w of up to vec_rows rows in shared memory
-cudaError_t fine_config(bool fp32, int NB, int vec_rows, LaunchCfg* cfg);
-size_t fine_smem(bool fp32, int NB, int threads, int vec_rows);
+// vec_rows > 0: each block keeps p, s, x (vec_count 3) or p, s, x, w (4) of up
+// to vec_rows rows in shared memory
+cudaError_t fine_config(bool fp32, int NB, int vec_rows, int vec_count, LaunchCfg* cfg);
+size_t fine_smem(bool fp32, int NB, int threads, int vec_rows, int vec_count);
 cudaError_t launch_fine_sweep(const FineArgs& a, bool fp32, const LaunchCfg& cfg, cudaStream_t st);
 // element data (c1, c2, s_a) of the nonlinear elements at the lanes of u
 void launch_elem_data(const MeshDev& m, int NB, const double* u, double* elem, cudaStream_t st);
