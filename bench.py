@@ -156,6 +156,25 @@ def cpu_baseline(prob, max_seconds=20.0):
                       f"{m.ndof} DOFs, from rest ({el:.1f} s)"}
 
 
+def aggregate(total_ms: float, units_per_step: float, steps: int):
+    """Whole-job rate of independent replicas: the work of all ranks divided
+    by the slowest rank's time (max over ranks).  Returns (value, t_max_ms)."""
+    world = 1
+    t_max = total_ms
+    try:
+        import torch
+        import torch.distributed as dist
+
+        if dist.is_available() and dist.is_initialized():
+            world = dist.get_world_size()
+            t = torch.tensor([total_ms], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_max = float(t.item())
+    except ImportError:
+        pass
+    return units_per_step * steps * world / (t_max * 1e-3), t_max
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -248,15 +267,7 @@ def main():
         torch.cuda.synchronize(dev)
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    t_max = total_ms
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = units_per_step * args.steps * world / (t_max * 1e-3)
+    value, t_max = aggregate(sum(step_ms), units_per_step, args.steps)
 
     # ---- roofline of the fine-propagator kernel (the dominant kernel)
     mc = solver.mesh_counts()

@@ -119,7 +119,7 @@ typedef struct pppc_stats {
 
 /* Fill *cfg with defaults: T=0.02, N=16, n_fine=20, FP64, averaged Jacobian,
  * tol_newton=1e-10, max_newton=30, tol_lin=1e-6, max_lin=20000,
- * tol_coarse=1e-10, max_coarse=20000, default stream, cudaMalloc,
+ * tol_coarse=1e-8, max_coarse=20000, default stream, cudaMalloc,
  * eta0=1e-2, predictor=1.  In PPPC_MIXED the PCG forcing term is at least
  * 1e-4 (an FP32 solve cannot refine further; Newton's FP64 residual does). */
 void pppc_config_default(pppc_config* cfg);

@@ -366,7 +366,7 @@ void pppc_config_default(pppc_config* c) {
     c->max_newton = 30;
     c->tol_lin = 1e-6;
     c->max_lin = 20000;
-    c->tol_coarse = 1e-10;
+    c->tol_coarse = 1e-8;
     c->max_coarse = 20000;
     c->eta0 = 1e-2;
     c->predictor = 1;

@@ -40,7 +40,7 @@ class PPPC:
 
     def __init__(self, T: float, N: int, n_fine: int, precision: str = "fp64",
                  coarse_lin: str = "avg_jacobian", tol_newton: float = 1e-10, max_newton: int = 30,
-                 tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-10,
+                 tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
                  max_coarse: int = 20000, eta0: float = 1e-2, predictor: bool = True, stream=None):
         self._lib = _lib.load()
         cfg = pppc_config()

@@ -1,0 +1,49 @@
+"""The bench's whole-job aggregation over independent replicas (2 gloo ranks
+on CPU): the value is the work of all ranks over the slowest rank's time."""
+
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    total_ms = 100.0 * (rank + 1)              # rank 1 is the slowest replica
+    value, t_max = bench.aggregate(total_ms, units_per_step=1000.0, steps=5)
+    out[rank] = (value, t_max)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_two_replicas():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        value, t_max = out[r]
+        assert t_max == pytest.approx(200.0)
+        assert value == pytest.approx(1000.0 * 5 * 2 / 0.2)
+
+
+def test_aggregate_single_process():
+    import bench
+
+    value, t_max = bench.aggregate(50.0, units_per_step=10.0, steps=4)
+    assert t_max == 50.0 and value == pytest.approx(10.0 * 4 / 0.05)
