@@ -63,6 +63,12 @@ typedef enum pppc_coarse_lin {
     PPPC_COARSE_ZERO_FIELD = 2    /* dK(U)U/dU at U = 0 */
 } pppc_coarse_lin;
 
+typedef enum pppc_method {
+    PPPC_METHOD_PPPC = 0, /* periodic coarse problem, multi-harmonic solve (Eq. 4, Eqs. 9-14) */
+    PPPC_METHOD_PPIC = 1  /* relaxed periodicity U_0^{k+1} = U_N^k with an initial-value coarse
+                             sweep (Eq. 5); the handle also keeps the end-of-period state U_N */
+} pppc_method;
+
 typedef enum pppc_nu_model {
     PPPC_NU_LINEAR = 0,  /* constant reluctivity nu */
     PPPC_NU_BRAUER = 1   /* nu(B^2) = k1 exp(k2 B^2) + k3 */
@@ -102,6 +108,7 @@ typedef struct pppc_config {
     double eta0;          /* PCG forcing term of each step's first Newton iteration; later ones
                              follow Eisenstat-Walker, 0.9 (|R_k|/|R_k-1|)^2, within [tol_lin, 0.1] */
     int32_t predictor;    /* 1: start each fine step's Newton from 2 u^m - u^{m-1} (default 1) */
+    int32_t method;       /* pppc_method (default PPPC_METHOD_PPPC) */
 } pppc_config;
 
 /* Iteration counts of the most recent iterate / solve / propagate call. */
@@ -154,7 +161,8 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
 pppc_status pppc_set_source(pppc_handle* h, int32_t n_harm, const double* amp, const double* freq,
                             const double* phase);
 
-/* Set / read the PP-PC state U_0..U_{N-1} (layout above). */
+/* Set / read the PP-PC state U_0..U_{N-1} (layout above).  With
+ * PPPC_METHOD_PPIC, set_state also sets the end-of-period state U_N to U_0. */
 pppc_status pppc_set_state(pppc_handle* h, const double* U, int32_t on_device);
 pppc_status pppc_get_state(pppc_handle* h, double* U, int32_t on_device);
 
@@ -169,11 +177,13 @@ pppc_status pppc_propagate_fine(pppc_handle* h, const double* U, double* F, int3
  * fine values F[j] = F_{j+1}(U^k_j), write U^{k+1} to U_new and
  * ||d|| / ||F|| of U^k (d_n = F_n - U_{n mod N}) to *rel_res (may be NULL).
  * Does not change the handle's state.  Errors: LINEAR, BREAKDOWN, TIMEOUT,
- * CUDA. */
+ * CUDA; UNSUPPORTED with PPPC_METHOD_PPIC (its update also needs U_N). */
 pppc_status pppc_coarse_update(pppc_handle* h, const double* U, const double* F, double* U_new,
                                double* rel_res, int32_t on_device);
 
-/* One PP-PC iteration (Eq. 4) on the handle's state: U^k -> U^{k+1}.
+/* One iteration on the handle's state, U^k -> U^{k+1}: PP-PC (Eq. 4), or
+ * PP-IC (Eq. 5) with PPPC_METHOD_PPIC, whose coarse sweep solves
+ * Q = M/dT + Kbar once per subinterval in sequence.
  * *rel_res (may be NULL) receives ||d|| / ||F|| of the incoming U^k. */
 pppc_status pppc_iterate(pppc_handle* h, double* rel_res);
 

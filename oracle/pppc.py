@@ -163,13 +163,29 @@ def pppc(model, N, n_fine, T, U0=None, tol=1e-12, kmax=50, coarse="harmonic",
     return res
 
 
+def ppic_update(model, U, F, N, T, lin="avg_jacobian"):
+    """One PP-IC coarse sweep (Eq. 5) on U = U_0..U_N (shape (N+1, ndof)),
+    given the fine results F_n = F(U_{n-1}), n = 1..N (shape (N, ndof)): the
+    new start value is the old end value, and each later value is the fine
+    result corrected by the coarse propagator's change, swept forward."""
+    dT = T / N
+    Q, C, _ = coarse_matrices(model, U[:N], N, T, lin)
+    Q_lu = spla.splu(Q.tocsc())
+    new = np.empty_like(U)
+    new[0] = U[N]
+    for n in range(1, N + 1):
+        fT = model.f(n * dT)
+        new[n] = (F[n - 1] + coarse_step(Q_lu, C, new[n - 1], fT)
+                  - coarse_step(Q_lu, C, U[n - 1], fT))
+    return new
+
+
 def ppic(model, N, n_fine, T, tol=1e-12, kmax=200, lin="avg_jacobian", **kw):
     """PP-IC: initial-value Parareal sweeps over one period with the relaxed
     periodicity U_0^{k+1} = U_N^k (Eq. 5).  The state holds U_0..U_N; its
     residual uses the same periodic jumps as PP-PC on U_0..U_{N-1}."""
     U = np.zeros((N + 1, model.ndof))
     res = PPResult(U=U, iterations=0, converged=False)
-    dT = T / N
     for k in range(kmax + 1):
         F = fine_sweep(model, U[:N], N, n_fine, T, **kw)
         res.history.append(rel_res(U[:N], F))
@@ -178,15 +194,7 @@ def ppic(model, N, n_fine, T, tol=1e-12, kmax=200, lin="avg_jacobian", **kw):
             return res
         if k == kmax:
             break
-        Q, C, _ = coarse_matrices(model, U[:N], N, T, lin)
-        Q_lu = spla.splu(Q.tocsc())
-        new = np.empty_like(U)
-        new[0] = U[N]
-        for n in range(1, N + 1):
-            fT = model.f(n * dT)
-            new[n] = (F[n - 1] + coarse_step(Q_lu, C, new[n - 1], fT)
-                      - coarse_step(Q_lu, C, U[n - 1], fT))
-        U = new
+        U = ppic_update(model, U, F, N, T, lin)
     res.U, res.iterations = U[:N], kmax
     return res
 

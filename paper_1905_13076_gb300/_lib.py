@@ -23,6 +23,7 @@ STATUS_NAMES = {
 }
 PPPC_FP64, PPPC_MIXED = 0, 1
 COARSE_LIN = {"avg_jacobian": 0, "avg_chord": 1, "zero_field": 2}
+METHODS = {"pppc": 0, "ppic": 1}
 NU_LINEAR, NU_BRAUER = 0, 1
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p)
@@ -36,6 +37,7 @@ class pppc_config(ctypes.Structure):
         ("tol_lin", c_double), ("max_lin", c_int32), ("tol_coarse", c_double),
         ("max_coarse", c_int32), ("stream", c_void_p), ("alloc", c_void_p),
         ("free_fn", c_void_p), ("alloc_ctx", c_void_p), ("eta0", c_double), ("predictor", c_int32),
+        ("method", c_int32),
     ]
 
 

@@ -61,7 +61,9 @@ struct pppc_handle {
     double* trace = nullptr; // Newton trace of the fine sweep (optional)
     int* trace_len = nullptr;
     int trace_cap = 0;
-    LaunchCfg fine_cfg, cocg_cfg;
+    LaunchCfg fine_cfg, cocg_cfg, cocg1_cfg;
+    // PP-IC: end-of-period state U_N (and its next value), sweep increment, shift 1 "twiddle"
+    double *UN = nullptr, *UNnext = nullptr, *dcur = nullptr, *tw_c1 = nullptr;
     bool coarse_fp32 = false;       // the harmonic solves run in FP64 in both precisions
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     SourceDev src{};
@@ -309,6 +311,73 @@ pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl,
     return PPPC_OK;
 }
 
+// PP-IC coarse sweep (Eq. 5): Unew and h->UNnext from Ul, Fl and h->UN.
+pppc_status run_ppic_sweep(pppc_handle* h, const double* Ul, const double* Fl, double* Unew) {
+    const int lin = h->cfg.coarse_lin;
+    CK(cudaEventRecord(h->ev[2], h->st));
+    if (lin != PPPC_COARSE_ZERO_FIELD && h->md.n_nl > 0) {
+        launch_elem_data(h->md, h->NB, Ul, h->elem, h->st);
+        h->stats.launches += 1;
+    }
+    if (h->md.n_slots > 0) {
+        launch_kbar(h->md, h->N, h->NB, lin, h->elem, h->Kbar, h->st);
+        h->stats.launches += 1;
+    }
+    const int ndof = h->hm.ndof;
+    launch_ppic_start(ndof, h->NB, Ul, h->UN, h->dcur, Unew, h->st);
+    h->stats.launches += 1;
+    CocgArgs c{};
+    c.mesh = h->md;
+    c.N = h->N;
+    c.H = 1;
+    c.inv_dT = 1.0 / h->dT;
+    c.tol = h->cfg.tol_coarse;
+    c.max_it = h->cfg.max_coarse;
+    c.Kbar = h->Kbar;
+    c.tw = h->tw_c1;  // shift c = 1: the matrix is Q = Kbar + M/dT
+    c.b = h->b;
+    c.x = h->cx;
+    c.r = h->cr;
+    c.z = h->cz;
+    c.w = h->cw;
+    c.p = h->cp;
+    c.s = h->cs;
+    c.invd_sp = h->cinvd;
+    c.part = h->part;
+    c.bar = h->bar;
+    c.status = h->status;
+    c.counters = h->counters;
+    for (int n = 1; n <= h->N; ++n) {
+        launch_ppic_rhs(h->md, 1.0 / h->dT, h->dcur, h->b, h->st);
+        CK(cudaGetLastError());
+        TRY(reset_control(h));
+        CK(launch_cocg(c, false, h->cocg1_cfg, h->st));
+        h->stats.launches += 2;
+        TRY(device_status(h, "PP-IC coarse step"));
+        launch_ppic_step(ndof, h->N, h->NB, n, Fl, Ul, h->UN, static_cast<const double*>(h->cx), h->dcur, Unew,
+                         h->UNnext, h->st);
+        h->stats.launches += 1;
+    }
+    launch_zero_pad_lanes(ndof, h->N, h->NB, Unew, h->st);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev[3], h->st));
+    CK(cudaEventSynchronize(h->ev[3]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+    h->stats.coarse_ms += ms;
+    return PPPC_OK;
+}
+
+pppc_status run_update(pppc_handle* h, const double* Ul, const double* Fl, double* Unew) {
+    if (h->cfg.method == PPPC_METHOD_PPIC) return run_ppic_sweep(h, Ul, Fl, Unew);
+    return run_coarse_solve(h, Ul, Fl, Unew);
+}
+
+void swap_state(pppc_handle* h) {
+    std::swap(h->U, h->Unext);
+    if (h->cfg.method == PPPC_METHOD_PPIC) std::swap(h->UN, h->UNnext);
+}
+
 pppc_status begin_call(pppc_handle* h) {
     CK(cudaMemsetAsync(h->counters, 0, 3 * sizeof(long long), h->st));
     h->stats = pppc_stats{};
@@ -370,6 +439,7 @@ void pppc_config_default(pppc_config* c) {
     c->max_coarse = 20000;
     c->eta0 = 1e-2;
     c->predictor = 1;
+    c->method = PPPC_METHOD_PPPC;
 }
 
 const char* pppc_status_string(pppc_status s) {
@@ -399,6 +469,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (c.coarse_lin < 0 || c.coarse_lin > 2) why = "unknown coarse_lin";
     else if (!(c.tol_newton > 0.0) || !(c.tol_lin > 0.0) || !(c.tol_coarse > 0.0)) why = "tolerances must be positive";
     else if (!(c.eta0 > 0.0) || !(c.eta0 < 1.0)) why = "eta0 must be in (0, 1)";
+    else if (c.method != PPPC_METHOD_PPPC && c.method != PPPC_METHOD_PPIC) why = "unknown method";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
@@ -678,6 +749,15 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     TRY(alloc_n(h, &h->counters, 3));
     TRY(alloc_n(h, &h->ext, (size_t)h->N * hm.n_nodes));
     CK(cudaMemsetAsync(h->U, 0, LV * sizeof(double), h->st));
+    if (h->cfg.method == PPPC_METHOD_PPIC) {
+        TRY(alloc_n(h, &h->UN, hm.ndof));
+        TRY(alloc_n(h, &h->UNnext, hm.ndof));
+        TRY(alloc_n(h, &h->dcur, hm.ndof));
+        TRY(alloc_n(h, &h->tw_c1, 2));
+        CK(cudaMemsetAsync(h->UN, 0, hm.ndof * sizeof(double), h->st));
+        CK(cudaMemsetAsync(h->tw_c1, 0, 2 * sizeof(double), h->st));
+        CK(cocg_config(false, 1, &h->cocg1_cfg));
+    }
     CK(cudaMemsetAsync(h->counters, 0, 3 * sizeof(long long), h->st));
     CK(cudaStreamSynchronize(h->st));
     h->has_mesh = true;
@@ -710,6 +790,9 @@ pppc_status pppc_set_state(pppc_handle* h, const double* U, int32_t on_device) {
     if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
     if (!U) return fail(h, PPPC_ERR_INVALID_ARG, "U is NULL");
     TRY(stage_in(h, U, on_device, h->U));
+    if (h->UN)  // PP-IC: the end-of-period state starts at U_0 (lane 0 of the lane layout)
+        CK(cudaMemcpy2DAsync(h->UN, sizeof(double), h->U, (size_t)h->NB * sizeof(double), sizeof(double),
+                             h->hm.ndof, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaStreamSynchronize(h->st));
     return PPPC_OK;
 }
@@ -736,6 +819,8 @@ pppc_status pppc_coarse_update(pppc_handle* h, const double* U, const double* F,
                                int32_t on_device) {
     TRY(need_ready(h));
     if (!U || !F || !U_new) return fail(h, PPPC_ERR_INVALID_ARG, "U, F or U_new is NULL");
+    if (h->cfg.method == PPPC_METHOD_PPIC)
+        return fail(h, PPPC_ERR_UNSUPPORTED, "pppc_coarse_update: PP-IC needs the end-of-period state");
     TRY(begin_call(h));
     // lanes: Unext <- U, F <- F (h->U, the handle's state, is untouched)
     TRY(stage_in(h, U, on_device, h->Unext));
@@ -751,9 +836,9 @@ pppc_status pppc_iterate(pppc_handle* h, double* rel_res) {
     TRY(begin_call(h));
     TRY(run_fine(h, h->U, h->F));
     TRY(run_jumps(h, h->U, h->F, rel_res));
-    TRY(run_coarse_solve(h, h->U, h->F, h->Unext));
+    TRY(run_update(h, h->U, h->F, h->Unext));
     CK(cudaStreamSynchronize(h->st));
-    std::swap(h->U, h->Unext);
+    swap_state(h);
     TRY(end_call(h));
     h->stats.fine_steps = h->cfg.n_fine;
     h->stats.pppc_iters = 1;
@@ -779,9 +864,9 @@ pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_
             return fail(h, PPPC_ERR_NOT_CONVERGED,
                         "rel_res " + std::to_string(rr) + " > tol after " + std::to_string(k) + " updates");
         }
-        TRY(run_coarse_solve(h, h->U, h->F, h->Unext));
+        TRY(run_update(h, h->U, h->F, h->Unext));
         CK(cudaStreamSynchronize(h->st));
-        std::swap(h->U, h->Unext);
+        swap_state(h);
     }
 }
 

@@ -344,6 +344,55 @@ size_t cocg_smem(int H, int threads) {
     return (size_t)(9 * H + CNV * RB * H + CNV * H + threads) * sizeof(double) + H * sizeof(int);
 }
 
+// ------------------------------------------------ PP-IC coarse sweep --
+// PP-IC (Eq. 5) relaxes periodicity to U_0^{k+1} = U_N^k and sweeps the
+// coarse propagator forward: with G linear within the iteration,
+//   D_0 = U_N^k - U_0^k,   D_n = (F_n - U_n^k) + Q^{-1} C D_{n-1},  n = 1..N,
+// and U_n^{k+1} = U_n^k + D_n (U_N^k being the stored end-of-period value).
+__global__ void ppic_start_kernel(int ndof, int NB, const double* U, const double* UN, double* dcur,
+                                  double* Unew) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) {
+        const double d0 = UN[i] - U[(size_t)i * NB];
+        dcur[i] = d0;
+        Unew[(size_t)i * NB] = U[(size_t)i * NB] + d0;
+    }
+}
+
+// b = C v on the special rows, as a one-harmonic complex right-hand side
+__global__ void ppic_rhs_kernel(MeshDev m, double inv_dT, const double* v, double* b) {
+    for (int sp = blockIdx.x * blockDim.x + threadIdx.x; sp < m.n_sp; sp += gridDim.x * blockDim.x) {
+        const int i = m.sp_rows[sp];
+        const int kb = m.rowptr[i], ke = m.rowptr[i + 1], slot0 = m.row_slot[i];
+        double acc = 0.0;
+        for (int k = kb; k < ke; ++k) acc += m.Mslot[slot0 + (k - kb)] * v[m.col[k]];
+        b[2 * (size_t)sp] = acc * inv_dT;
+        b[2 * (size_t)sp + 1] = 0.0;
+    }
+}
+
+// D_n = (F_n - U_n) + Re x;  U_n^{k+1} = U_n + D_n (n < N) or U_N^{k+1} = U_N + D_N
+__global__ void ppic_step_kernel(int ndof, int N, int NB, int n, const double* F, const double* U, const double* UN,
+                                 const double* x, double* dcur, double* Unew, double* UNnew) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndof; i += gridDim.x * blockDim.x) {
+        const double Un = n < N ? U[(size_t)i * NB + n] : UN[i];
+        const double dn = (F[(size_t)i * NB + (n - 1)] - Un) + x[2 * (size_t)i];
+        dcur[i] = dn;
+        if (n < N)
+            Unew[(size_t)i * NB + n] = Un + dn;
+        else
+            UNnew[i] = Un + dn;
+    }
+}
+
+__global__ void zero_pad_lanes_kernel(int ndof, int N, int NB, double* U) {
+    const long long total = (long long)ndof * (NB - N);
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x) {
+        const long long i = it / (NB - N);
+        U[i * NB + N + (it % (NB - N))] = 0.0;
+    }
+}
+
 // ------------------------------------------------ inverse DFT + update --
 // U_n^{k+1} = F_n(U_{n-1}^k) + (1/N) sum_{p in P} W_p exp(i 2 pi p n / N),
 // the sum taken over the Hermitian spectrum from p = 0..N/2.
@@ -420,7 +469,7 @@ void launch_coarse_rhs(const MeshDev& m, int N, int NB, int H, double inv_dT, co
 }
 
 cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg) {
-    if (H < 2 || H > 512) return cudaErrorInvalidValue;
+    if (H < 1 || H > 512) return cudaErrorInvalidValue;
     const int threads = H * (512 / H);
     const size_t smem = cocg_smem(H, threads);
     const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
@@ -442,6 +491,26 @@ cudaError_t launch_cocg(const CocgArgs& a, bool fp32, const LaunchCfg& cfg, cuda
     void* args[] = {const_cast<CocgArgs*>(&a)};
     const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
     return cudaLaunchCooperativeKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+void launch_ppic_start(int ndof, int NB, const double* U, const double* UN, double* dcur, double* Unew,
+                       cudaStream_t st) {
+    ppic_start_kernel<<<grid_for(ndof, 256), 256, 0, st>>>(ndof, NB, U, UN, dcur, Unew);
+}
+
+void launch_ppic_rhs(const MeshDev& m, double inv_dT, const double* v, double* b, cudaStream_t st) {
+    if (m.n_sp == 0) return;
+    ppic_rhs_kernel<<<grid_for(m.n_sp, 256), 256, 0, st>>>(m, inv_dT, v, b);
+}
+
+void launch_ppic_step(int ndof, int N, int NB, int n, const double* F, const double* U, const double* UN,
+                      const double* x, double* dcur, double* Unew, double* UNnew, cudaStream_t st) {
+    ppic_step_kernel<<<grid_for(ndof, 256), 256, 0, st>>>(ndof, N, NB, n, F, U, UN, x, dcur, Unew, UNnew);
+}
+
+void launch_zero_pad_lanes(int ndof, int N, int NB, double* U, cudaStream_t st) {
+    if (NB == N) return;
+    zero_pad_lanes_kernel<<<grid_for((long long)ndof * (NB - N), 256), 256, 0, st>>>(ndof, N, NB, U);
 }
 
 void launch_idft_update(int ndof, int N, int NB, int H, bool fp32, const void* W, const double* F,

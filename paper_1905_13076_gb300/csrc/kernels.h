@@ -62,6 +62,13 @@ void launch_coarse_rhs(const MeshDev& m, int N, int NB, int H, double inv_dT, co
                        const double* tw, double* y, double* b, cudaStream_t st);
 cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg);
 cudaError_t launch_cocg(const CocgArgs& a, bool fp32, const LaunchCfg& cfg, cudaStream_t st);
+// PP-IC coarse sweep (Eq. 5): start, right-hand side C v, one step n
+void launch_ppic_start(int ndof, int NB, const double* U, const double* UN, double* dcur, double* Unew,
+                       cudaStream_t st);
+void launch_ppic_rhs(const MeshDev& m, double inv_dT, const double* v, double* b, cudaStream_t st);
+void launch_ppic_step(int ndof, int N, int NB, int n, const double* F, const double* U, const double* UN,
+                      const double* x, double* dcur, double* Unew, double* UNnew, cudaStream_t st);
+void launch_zero_pad_lanes(int ndof, int N, int NB, double* U, cudaStream_t st);
 void launch_idft_update(int ndof, int N, int NB, int H, bool fp32, const void* W, const double* F,
                         const double* tw, double* Unew, cudaStream_t st);
 

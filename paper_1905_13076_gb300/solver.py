@@ -41,7 +41,8 @@ class PPPC:
     def __init__(self, T: float, N: int, n_fine: int, precision: str = "fp64",
                  coarse_lin: str = "avg_jacobian", tol_newton: float = 1e-10, max_newton: int = 30,
                  tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
-                 max_coarse: int = 20000, eta0: float = 1e-2, predictor: bool = True, stream=None):
+                 max_coarse: int = 20000, eta0: float = 1e-2, predictor: bool = True, method: str = "pppc",
+                 stream=None):
         self._lib = _lib.load()
         cfg = pppc_config()
         self._lib.pppc_config_default(ctypes.byref(cfg))
@@ -52,6 +53,7 @@ class PPPC:
         cfg.tol_lin, cfg.max_lin = float(tol_lin), int(max_lin)
         cfg.tol_coarse, cfg.max_coarse = float(tol_coarse), int(max_coarse)
         cfg.eta0, cfg.predictor = float(eta0), int(bool(predictor))
+        cfg.method = _lib.METHODS[method]
         cfg.stream = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
         self.cfg = cfg
         h = ctypes.c_void_p()
