@@ -63,6 +63,17 @@ typedef enum pppc_coarse_lin {
     PPPC_COARSE_ZERO_FIELD = 2    /* dK(U)U/dU at U = 0 */
 } pppc_coarse_lin;
 
+/* The frozen coarse stiffness Kbar^k (Eq. 8 with a nonlinear K; the paper
+ * leaves it open) is averaged over the N coarse points of the period, taken
+ * either at the iterate U_n^k or at the fine results F_n^k.  At the fixed
+ * point the two coincide.  The fine results come from physical time
+ * stepping, so they keep Kbar meaningful when U^k is far from any
+ * physical state (a cold start of a strongly nonlinear cable). */
+typedef enum pppc_coarse_at {
+    PPPC_COARSE_AT_U = 0,
+    PPPC_COARSE_AT_F = 1
+} pppc_coarse_at;
+
 typedef enum pppc_method {
     PPPC_METHOD_PPPC = 0, /* periodic coarse problem, multi-harmonic solve (Eq. 4, Eqs. 9-14) */
     PPPC_METHOD_PPIC = 1  /* relaxed periodicity U_0^{k+1} = U_N^k with an initial-value coarse
@@ -81,6 +92,10 @@ typedef struct pppc_material {
     double nu;          /* reluctivity [m/H] for PPPC_NU_LINEAR, > 0 */
     double k1, k2, k3;  /* Brauer constants for PPPC_NU_BRAUER, k1,k3 > 0, k2 >= 0 */
     int32_t is_source;  /* 1: carries the impressed current I(t) uniformly */
+    double bmax;        /* Brauer only: |B| [T] past which nu(b), b = |B|^2, continues along
+                           its tangent at b = bmax^2 instead of exponentially (the fit has
+                           no meaning past saturation and overflows on far-off Newton or
+                           coarse iterates); nu and nu' stay continuous; 0: no cap */
 } pppc_material;
 
 /* Opaque handle: one problem (mesh, materials, source, time grid, state). */
@@ -109,6 +124,7 @@ typedef struct pppc_config {
                              follow Eisenstat-Walker, 0.9 (|R_k|/|R_k-1|)^2, within [tol_lin, 0.1] */
     int32_t predictor;    /* 1: start each fine step's Newton from 2 u^m - u^{m-1} (default 1) */
     int32_t method;       /* pppc_method (default PPPC_METHOD_PPPC) */
+    int32_t coarse_at;    /* pppc_coarse_at: where the coarse stiffness is frozen (default U^k) */
 } pppc_config;
 
 /* Iteration counts of the most recent iterate / solve / propagate call. */
@@ -122,6 +138,8 @@ typedef struct pppc_stats {
     double fine_ms;          /* device time of the fine-propagator launches (CUDA events) */
     double coarse_ms;        /* device time of the coarse kernels (jumps .. update) */
     int64_t launches;        /* kernels this library launched during the call */
+    int64_t backtracks;      /* Newton rounds of the fine sweeps in which some lane halved its step
+                                because the residual did not drop (0 on well-behaved problems) */
 } pppc_stats;
 
 /* Fill *cfg with defaults: T=0.02, N=16, n_fine=20, FP64, averaged Jacobian,
@@ -264,6 +282,74 @@ const char* pppc_last_error(pppc_handle* h);
 
 /* Static name of a status code. */
 const char* pppc_status_string(pppc_status s);
+
+/* ---- Many independent problems in one launch ------------------------------
+ * The paper solves one problem at a time.  A batch runs PP-PC (Eq. 4 with the
+ * multi-harmonic coarse solve, Eqs. 11-14) on many independent problems --
+ * cables of different meshes, materials, sources, N and n_fine -- at once.
+ * Each batch iteration runs two captured CUDA graphs:
+ *   1. one cooperative launch in which every active member's fine sweep runs
+ *      on its own team of blocks (each team has its own grid barrier and
+ *      reductions), then every member's jumps;
+ *   2. every member's coarse linearisation and right-hand side, one
+ *      cooperative launch of all members' harmonic solves (again one team per
+ *      member), and every member's inverse DFT + update.
+ * Team sizes start from a cost model (rows x lanes x fine steps) and, with
+ * autotune = 1, are re-balanced from the per-team times the kernels measure
+ * (%globaltimer) whenever that shortens the predicted launch by more than
+ * 10%; the graphs are captured again after every change of teams or of the
+ * set of active members.
+ *
+ * Members are handles that already have a mesh, a source and a state, all
+ * with the same precision, the PP-PC method, the same stream (cfg.stream)
+ * and NB / (4 FP32 or 2 FP64 lanes) a power of two (e.g. N = 16, 32, 64).
+ * At most one member per SM.  The batch uses the members' own workspaces and
+ * states: pppc_get_state on a member reads its current U^k.  The batch runs
+ * its graphs on a stream of its own; each batch call first synchronises the
+ * members' stream and returns once its work is complete.  While the batch
+ * exists, the members must not be used on their own or in another batch.
+ * Destroy the batch before its members.
+ *
+ * Errors of pppc_batch_create: INVALID_ARG (count < 1, NULL member,
+ * duplicate), STATE (member without mesh, source), UNSUPPORTED (mixed
+ * precisions or streams, PP-IC, a lane count that is not a power of two,
+ * count > SMs), CUDA, NOMEM.  The message is in pppc_batch_last_error(NULL)
+ * after a failed create. */
+typedef struct pppc_batch pppc_batch;
+
+typedef struct pppc_batch_stats {
+    int32_t iterations;        /* batch iterations run by the last call */
+    int32_t retunes;           /* team re-partitions made by the tuner during the last call */
+    int64_t graph_launches;    /* CUDA graph launches of the last call */
+    int64_t kernel_launches;   /* kernels launched inside those graphs */
+    int64_t fine_dof_steps;    /* sum over members and iterations of N * n_fine * ndof */
+    double fine_ms;            /* device time of the fine-sweep graphs */
+    double coarse_ms;          /* device time of the coarse graphs */
+} pppc_batch_stats;
+
+pppc_status pppc_batch_create(pppc_handle* const* members, int32_t count, int32_t autotune, pppc_batch** out);
+void pppc_batch_destroy(pppc_batch* b);
+
+/* One PP-PC iteration on every member: rel_res[count] (may be NULL) gets each
+ * member's ||d|| / ||F|| of its incoming U^k. */
+pppc_status pppc_batch_iterate(pppc_batch* b, double* rel_res);
+
+/* Iterate every member until its rel_res <= tol (its state is then the first
+ * U^k that passed and it stops iterating) or kmax updates are done.
+ * iters[count] and rel_res[count] (each may be NULL) get every member's
+ * update count and final residual.  Returns NOT_CONVERGED if any member did
+ * not reach tol (all results are still written), else the first error of
+ * any member (the message names it). */
+pppc_status pppc_batch_solve_periodic(pppc_batch* b, double tol, int32_t kmax, int32_t* iters, double* rel_res);
+
+pppc_status pppc_batch_get_stats(pppc_batch* b, pppc_batch_stats* out);
+
+/* Current team sizes (blocks) of each member in the fine and coarse
+ * launches: fine_blocks[count], cocg_blocks[count] (each may be NULL). */
+pppc_status pppc_batch_get_teams(pppc_batch* b, int32_t* fine_blocks, int32_t* cocg_blocks);
+
+/* Last error on b, or of the last failed pppc_batch_create when b is NULL. */
+const char* pppc_batch_last_error(pppc_batch* b);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,9 @@ functions of a triangle e of area |e|:
 * stiffness ("curl-curl") for a linear material:
       K_ab = sum_e nu_e |e| grad N_a . grad N_b
 * nonlinear material, nu = nu(|B|^2) with |B|^2 = |grad A|^2 on each element
-  (Brauer law nu = k1 exp(k2 b) + k3):
+  (Brauer law nu = k1 exp(k2 b) + k3; when a cap bmax > 0 is given, it is
+  continued past b_c = bmax^2 by its tangent in b,
+  nu = k1 exp(k2 b_c) (1 + k2 (b - b_c)) + k3, so nu and nu' stay continuous):
       (K(u) u)_a = sum_e |e| nu(b_e) grad N_a . grad A_e
   and its Jacobian
       J_ab = sum_e |e| [ nu grad N_a . grad N_b
@@ -75,6 +77,8 @@ class FEModel:
         self.linear = np.nonzero(model == NU_LINEAR)[0]
         self.nu_lin = np.asarray(problem.nu, dtype=np.float64)[region]
         self.k = np.asarray(problem.brauer, dtype=np.float64)[region]      # (n_tri, 3)
+        bmax = np.asarray(getattr(problem, "bmax", np.zeros(len(problem.brauer))), dtype=np.float64)[region]
+        self.b2max = np.where(bmax > 0.0, bmax * bmax, np.inf)             # (n_tri,)
         self.sigma = sigma
 
         # element matrices -> global COO over all nodes, then restrict to free dofs
@@ -123,12 +127,13 @@ class FEModel:
 
     def nu_brauer(self, b2, elems):
         k = self.k[elems]
-        return k[:, 0] * np.exp(k[:, 1] * b2) + k[:, 2]
+        bc = np.minimum(b2, self.b2max[elems])
+        return k[:, 0] * np.exp(k[:, 1] * bc) * (1.0 + k[:, 1] * (b2 - bc)) + k[:, 2]
 
     def dnu_brauer(self, b2, elems):
-        """d nu / d(B^2)."""
+        """d nu / d(B^2) (constant past the cap)."""
         k = self.k[elems]
-        return k[:, 0] * k[:, 1] * np.exp(k[:, 1] * b2)
+        return k[:, 0] * k[:, 1] * np.exp(k[:, 1] * np.minimum(b2, self.b2max[elems]))
 
     # -- operators ----------------------------------------------------------
     def Ku(self, u):

@@ -125,9 +125,12 @@ def rel_res(U, F):
     return float(np.linalg.norm(jumps(U, F)) / np.linalg.norm(F))
 
 
-def coarse_update(model, U, F, N, T, coarse="harmonic", lin="avg_jacobian"):
-    """Steps 3-5 of one PP-PC iteration: U^{k+1} from U^k and F^k (F[j] = F_{j+1})."""
-    Q, C, _ = coarse_matrices(model, U, N, T, lin)
+def coarse_update(model, U, F, N, T, coarse="harmonic", lin="avg_jacobian", at="U"):
+    """Steps 3-5 of one PP-PC iteration: U^{k+1} from U^k and F^k (F[j] = F_{j+1}).
+    The frozen coarse stiffness is taken at the states U_n^k (at="U") or at
+    the fine results F_n^k (at="F"); both sets are the N coarse points of the
+    period, and at the fixed point they coincide."""
+    Q, C, _ = coarse_matrices(model, U if at == "U" else F, N, T, lin)
     Q_lu = spla.splu(Q.tocsc())
     dT = T / N
     r = np.empty_like(U)
@@ -143,7 +146,7 @@ def coarse_update(model, U, F, N, T, coarse="harmonic", lin="avg_jacobian"):
 
 
 def pppc(model, N, n_fine, T, U0=None, tol=1e-12, kmax=50, coarse="harmonic",
-         lin="avg_jacobian", keep_states=False, **kw):
+         lin="avg_jacobian", keep_states=False, at="U", **kw):
     """PP-PC (Eq. 4) until rel_res(U^k) <= tol.  ``iterations`` is the number k
     of completed updates when the test first passes; ``U`` is that U^k."""
     U = np.zeros((N, model.ndof)) if U0 is None else np.array(U0, dtype=np.float64, copy=True)
@@ -158,18 +161,18 @@ def pppc(model, N, n_fine, T, U0=None, tol=1e-12, kmax=50, coarse="harmonic",
             return res
         if k == kmax:
             break
-        U = coarse_update(model, U, F, N, T, coarse, lin)
+        U = coarse_update(model, U, F, N, T, coarse, lin, at)
     res.U, res.iterations = U, kmax
     return res
 
 
-def ppic_update(model, U, F, N, T, lin="avg_jacobian"):
+def ppic_update(model, U, F, N, T, lin="avg_jacobian", at="U"):
     """One PP-IC coarse sweep (Eq. 5) on U = U_0..U_N (shape (N+1, ndof)),
     given the fine results F_n = F(U_{n-1}), n = 1..N (shape (N, ndof)): the
     new start value is the old end value, and each later value is the fine
     result corrected by the coarse propagator's change, swept forward."""
     dT = T / N
-    Q, C, _ = coarse_matrices(model, U[:N], N, T, lin)
+    Q, C, _ = coarse_matrices(model, U[:N] if at == "U" else F, N, T, lin)
     Q_lu = spla.splu(Q.tocsc())
     new = np.empty_like(U)
     new[0] = U[N]
@@ -180,7 +183,7 @@ def ppic_update(model, U, F, N, T, lin="avg_jacobian"):
     return new
 
 
-def ppic(model, N, n_fine, T, tol=1e-12, kmax=200, lin="avg_jacobian", **kw):
+def ppic(model, N, n_fine, T, tol=1e-12, kmax=200, lin="avg_jacobian", at="U", **kw):
     """PP-IC: initial-value Parareal sweeps over one period with the relaxed
     periodicity U_0^{k+1} = U_N^k (Eq. 5).  The state holds U_0..U_N; its
     residual uses the same periodic jumps as PP-PC on U_0..U_{N-1}."""
@@ -194,7 +197,7 @@ def ppic(model, N, n_fine, T, tol=1e-12, kmax=200, lin="avg_jacobian", **kw):
             return res
         if k == kmax:
             break
-        U = ppic_update(model, U, F, N, T, lin)
+        U = ppic_update(model, U, F, N, T, lin, at)
     res.U, res.iterations = U[:N], kmax
     return res
 

@@ -6,4 +6,4 @@ The compute path is the CUDA library ``libpppc.so`` (C ABI in
 """
 
 from ._lib import PPPCError, load  # noqa: F401
-from .solver import PPPC, Material, from_problem  # noqa: F401
+from .solver import PPPC, Material, PPPCBatch, from_problem  # noqa: F401

@@ -24,6 +24,7 @@ STATUS_NAMES = {
 PPPC_FP64, PPPC_MIXED = 0, 1
 COARSE_LIN = {"avg_jacobian": 0, "avg_chord": 1, "zero_field": 2}
 METHODS = {"pppc": 0, "ppic": 1}
+COARSE_AT = {"U": 0, "F": 1}
 NU_LINEAR, NU_BRAUER = 0, 1
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p)
@@ -37,14 +38,14 @@ class pppc_config(ctypes.Structure):
         ("tol_lin", c_double), ("max_lin", c_int32), ("tol_coarse", c_double),
         ("max_coarse", c_int32), ("stream", c_void_p), ("alloc", c_void_p),
         ("free_fn", c_void_p), ("alloc_ctx", c_void_p), ("eta0", c_double), ("predictor", c_int32),
-        ("method", c_int32),
+        ("method", c_int32), ("coarse_at", c_int32),
     ]
 
 
 class pppc_material(ctypes.Structure):
     _fields_ = [
         ("sigma", c_double), ("nu_model", c_int32), ("nu", c_double),
-        ("k1", c_double), ("k2", c_double), ("k3", c_double), ("is_source", c_int32),
+        ("k1", c_double), ("k2", c_double), ("k3", c_double), ("is_source", c_int32), ("bmax", c_double),
     ]
 
 
@@ -52,13 +53,19 @@ class pppc_stats(ctypes.Structure):
     _fields_ = [
         ("newton_iters", c_int64), ("pcg_iters", c_int64), ("cocg_iters", c_int64),
         ("fine_steps", c_int64), ("pppc_iters", c_int32), ("rel_res", c_double),
-        ("fine_ms", c_double), ("coarse_ms", c_double), ("launches", c_int64),
+        ("fine_ms", c_double), ("coarse_ms", c_double), ("launches", c_int64), ("backtracks", c_int64),
     ]
 
 
 class pppc_mesh_counts(ctypes.Structure):
     _fields_ = [("ndof", c_int64), ("nnz", c_int64), ("special_rows", c_int64),
                 ("special_entries", c_int64), ("nonlinear_elems", c_int64)]
+
+
+class pppc_batch_stats(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("retunes", c_int32), ("graph_launches", c_int64),
+                ("kernel_launches", c_int64), ("fine_dof_steps", c_int64), ("fine_ms", c_double),
+                ("coarse_ms", c_double)]
 
 
 _DPTR = POINTER(c_double)
@@ -87,6 +94,13 @@ SIGNATURES = {
     "pppc_status_string": (c_char_p, [c_int32]),
     "pppc_harmonic_solve_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                               c_void_p, c_void_p, c_double, c_int32, c_void_p, _IPTR]),
+    "pppc_batch_create": (c_int32, [POINTER(c_void_p), c_int32, c_int32, POINTER(c_void_p)]),
+    "pppc_batch_destroy": (None, [c_void_p]),
+    "pppc_batch_iterate": (c_int32, [c_void_p, _DPTR]),
+    "pppc_batch_solve_periodic": (c_int32, [c_void_p, c_double, c_int32, _IPTR, _DPTR]),
+    "pppc_batch_get_stats": (c_int32, [c_void_p, POINTER(pppc_batch_stats)]),
+    "pppc_batch_get_teams": (c_int32, [c_void_p, _IPTR, _IPTR]),
+    "pppc_batch_last_error": (c_char_p, [c_void_p]),
 }
 
 _lib = None
@@ -122,4 +136,11 @@ def check(status: int, handle=None):
     if status != PPPC_OK:
         lib = load()
         msg = lib.pppc_last_error(handle)
+        raise PPPCError(status, msg.decode() if msg else "")
+
+
+def check_batch(status: int, batch=None):
+    if status != PPPC_OK:
+        lib = load()
+        msg = lib.pppc_batch_last_error(batch)
         raise PPPCError(status, msg.decode() if msg else "")

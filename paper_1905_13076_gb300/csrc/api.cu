@@ -13,10 +13,12 @@
 
 #include "../../include/pppc.h"
 #include "args.h"
+#include "handle.h"
 #include "kernels.h"
 #include "mesh_host.h"
 
 using namespace pppc;
+using namespace pppc::detail;
 
 namespace {
 thread_local std::string g_create_error;
@@ -26,50 +28,6 @@ thread_local std::string g_create_error;
 constexpr double kFp32KrylovFloor = 1e-4;
 }
 
-struct pppc_handle {
-    pppc_config cfg{};
-    cudaStream_t st = nullptr;
-    std::string err;
-    bool has_mesh = false, has_source = false;
-    int N = 0, NB = 0, H = 0;
-    double dt = 0.0, dT = 0.0;
-    bool fp32 = false;
-    HostMesh hm;
-    std::vector<void*> allocs;   // everything allocated for the current mesh
-    MeshDev md{};
-    int* d_node_of_dof = nullptr;
-    int* d_dof_of_node = nullptr;
-    int* d_row_start = nullptr;     // [fine blocks + 1] rows owned by each block of the fine sweep
-    int* d_long_start = nullptr;    // [fine blocks + 1]
-    int* d_long_rows = nullptr;     // rows with more than 32 nonzeros, by owning block
-    int vec_rows = 0;               // > 0: fine-sweep vectors p, s, x kept in shared memory
-    int vec_w = 0;                  // 1: and w
-    // lane vectors [ndof][NB]
-    double *U = nullptr, *Unext = nullptr, *F = nullptr, *uprev = nullptr, *d = nullptr;
-    double* elem = nullptr;
-    void *r = nullptr, *z = nullptr, *w = nullptr, *p = nullptr, *s = nullptr, *x = nullptr, *J = nullptr,
-         *invd = nullptr;
-    // coarse
-    double *y = nullptr, *b = nullptr, *Kbar = nullptr, *tw = nullptr;
-    void *cx = nullptr, *cr = nullptr, *cz = nullptr, *cw = nullptr, *cp = nullptr, *cs = nullptr, *cinvd = nullptr;
-    // reductions and control
-    double *part = nullptr, *jsums = nullptr, *scalars = nullptr;
-    GridBarrier* bar = nullptr;
-    int* status = nullptr;
-    long long* counters = nullptr;
-    double* ext = nullptr;   // [N][n_nodes] staging for host states
-    double* trace = nullptr; // Newton trace of the fine sweep (optional)
-    int* trace_len = nullptr;
-    int trace_cap = 0;
-    LaunchCfg fine_cfg, cocg_cfg, cocg1_cfg;
-    // PP-IC: end-of-period state U_N (and its next value), sweep increment, shift 1 "twiddle"
-    double *UN = nullptr, *UNnext = nullptr, *dcur = nullptr, *tw_c1 = nullptr;
-    bool coarse_fp32 = false;       // the harmonic solves run in FP64 in both precisions
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    SourceDev src{};
-    double gnorm = 0.0, src_area = 0.0;
-    pppc_stats stats{};
-};
 
 namespace {
 
@@ -86,10 +44,14 @@ const char* kStatusNames[] = {"PPPC_OK",
                               "PPPC_ERR_UNSUPPORTED",
                               "PPPC_ERR_NOMEM"};
 
-pppc_status fail(pppc_handle* h, pppc_status s, const std::string& msg) {
+}  // namespace
+
+pppc_status pppc::detail::fail(pppc_handle* h, pppc_status s, const std::string& msg) {
     h->err = msg;
     return s;
 }
+
+namespace {
 
 #define CK(call)                                                                              \
     do {                                                                                      \
@@ -144,7 +106,9 @@ pppc_status upload(pppc_handle* h, T** out, const std::vector<T>& v) {
     return PPPC_OK;
 }
 
-pppc_status device_status(pppc_handle* h, const char* where) {
+}  // namespace
+
+pppc_status pppc::detail::device_status(pppc_handle* h, const char* where) {
     CK(cudaStreamSynchronize(h->st));
     int code = 0;
     CK(cudaMemcpy(&code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -160,6 +124,8 @@ pppc_status device_status(pppc_handle* h, const char* where) {
         default: return fail(h, PPPC_ERR_CUDA, w + ": unknown device status " + std::to_string(code));
     }
 }
+
+namespace {
 
 pppc_status reset_control(pppc_handle* h) {
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
@@ -181,6 +147,27 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
     const size_t lane_bytes = (size_t)h->hm.ndof * h->NB * sizeof(double);
     CK(cudaMemcpyAsync(Fout, Uin, lane_bytes, cudaMemcpyDeviceToDevice, h->st));
     TRY(reset_control(h));
+    FineArgs a = fine_args(h, Fout);
+    if (h->trace_cap > 0) {
+        CK(cudaMemsetAsync(h->trace_len, 0, sizeof(int), h->st));
+        a.trace = h->trace;
+        a.trace_cap = h->trace_cap;
+        a.trace_len = h->trace_len;
+    }
+    CK(cudaEventRecord(h->ev[0], h->st));
+    CK(launch_fine_sweep(a, h->fp32, h->fine_cfg, h->st));
+    h->stats.launches += 1;
+    CK(cudaEventRecord(h->ev[1], h->st));
+    TRY(device_status(h, "fine propagators"));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+    h->stats.fine_ms += ms;
+    return PPPC_OK;
+}
+
+}  // namespace
+
+FineArgs pppc::detail::fine_args(pppc_handle* h, double* Fout) {
     FineArgs a{};
     a.mesh = h->md;
     a.src = h->src;
@@ -198,6 +185,7 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
     a.eta0 = std::max(h->cfg.eta0, a.tol_lin);
     a.predictor = h->cfg.predictor;
     a.x = h->x;
+    a.dx = h->dx;
     a.max_newton = h->cfg.max_newton;
     a.max_lin = h->cfg.max_lin;
     a.u = Fout;
@@ -219,22 +207,85 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
     a.bar = h->bar;
     a.status = h->status;
     a.counters = h->counters;
-    if (h->trace_cap > 0) {
-        CK(cudaMemsetAsync(h->trace_len, 0, sizeof(int), h->st));
-        a.trace = h->trace;
-        a.trace_cap = h->trace_cap;
-        a.trace_len = h->trace_len;
-    }
-    CK(cudaEventRecord(h->ev[0], h->st));
-    CK(launch_fine_sweep(a, h->fp32, h->fine_cfg, h->st));
-    h->stats.launches += 1;
-    CK(cudaEventRecord(h->ev[1], h->st));
-    TRY(device_status(h, "fine propagators"));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
-    h->stats.fine_ms += ms;
-    return PPPC_OK;
+    return a;
 }
+
+CocgArgs pppc::detail::cocg_args(pppc_handle* h) {
+    CocgArgs c{};
+    c.mesh = h->md;
+    c.N = h->N;
+    c.H = h->H;
+    c.inv_dT = 1.0 / h->dT;
+    // FP32 Krylov recurrences cannot resolve FP64-level tolerances; an inexact
+    // coarse solve only slows PP-PC (its fixed point does not depend on it).
+    c.tol = h->coarse_fp32 ? std::max(h->cfg.tol_coarse, kFp32KrylovFloor) : h->cfg.tol_coarse;
+    c.max_it = h->cfg.max_coarse;
+    c.Kbar = h->Kbar;
+    c.tw = h->tw;
+    c.b = h->b;
+    c.x = h->cx;
+    c.r = h->cr;
+    c.z = h->cz;
+    c.w = h->cw;
+    c.p = h->cp;
+    c.s = h->cs;
+    c.invd_sp = h->cinvd;
+    c.part = h->part;
+    c.bar = h->bar;
+    c.status = h->status;
+    c.counters = h->counters;
+    return c;
+}
+
+void pppc::detail::partition_rows(const HostMesh& hm, int nb, std::vector<int>& rs, std::vector<int>& ls,
+                                  std::vector<int>& lrows, int* rows_max) {
+    std::vector<double> cum(hm.ndof + 1, 0.0);
+    for (int i = 0; i < hm.ndof; ++i) {
+        const int nz = hm.rowptr[i + 1] - hm.rowptr[i];
+        cum[i + 1] = cum[i] + 2.0 + nz * (hm.row_slot[i] >= 0 ? 2.0 : 1.0) + (nz > 32 ? 400.0 : 0.0);
+    }
+    rs.assign(nb + 1, hm.ndof);
+    rs[0] = 0;
+    int i = 0;
+    for (int b = 1; b < nb; ++b) {
+        const double target = cum[hm.ndof] * b / nb;
+        while (i < hm.ndof && cum[i] < target) ++i;
+        rs[b] = i;
+    }
+    *rows_max = 0;
+    for (int b = 0; b < nb; ++b) *rows_max = std::max(*rows_max, rs[b + 1] - rs[b]);
+    ls.assign(nb + 1, 0);
+    lrows.clear();
+    for (int b = 0; b < nb; ++b) {
+        for (int r = rs[b]; r < rs[b + 1]; ++r)
+            if (hm.rowptr[r + 1] - hm.rowptr[r] > 32) lrows.push_back(r);
+        ls[b + 1] = (int)lrows.size();
+    }
+}
+
+double pppc::detail::fine_cost_estimate(const pppc_handle* h) {
+    const HostMesh& hm = h->hm;
+    double c = 0.0;
+    for (int i = 0; i < hm.ndof; ++i) {
+        const int nz = hm.rowptr[i + 1] - hm.rowptr[i];
+        c += 2.0 + nz * (hm.row_slot[i] >= 0 ? 2.0 : 1.0);
+    }
+    return c * h->NB * h->cfg.n_fine;
+}
+
+void pppc::detail::choose_vec_rows(bool fp32, int NB, int rows_max, size_t budget, int* vec_rows, int* vec_w) {
+    const int V = fp32 ? 4 : 2, G = NB / V, threads = G * (1024 / G);
+    *vec_rows = 0;
+    *vec_w = 0;
+    if (fine_smem(fp32, NB, threads, rows_max, 4) <= budget) {
+        *vec_rows = rows_max;
+        *vec_w = 1;
+    } else if (fine_smem(fp32, NB, threads, rows_max, 3) <= budget) {
+        *vec_rows = rows_max;
+    }
+}
+
+namespace {
 
 // jumps d and ||d||^2, ||F||^2 into h->jsums
 pppc_status run_jumps(pppc_handle* h, const double* Ul, const double* Fl, double* rel_res) {
@@ -261,7 +312,7 @@ pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl,
     const int lin = h->cfg.coarse_lin;
     CK(cudaEventRecord(h->ev[2], h->st));
     if (lin != PPPC_COARSE_ZERO_FIELD && h->md.n_nl > 0) {
-        launch_elem_data(h->md, h->NB, Ul, h->elem, h->st);
+        launch_elem_data(h->md, h->NB, h->cfg.coarse_at == PPPC_COARSE_AT_F ? Fl : Ul, h->elem, h->st);
         h->stats.launches += 1;
     }
     if (h->md.n_slots > 0) {
@@ -274,29 +325,7 @@ pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl,
     }
     CK(cudaGetLastError());
     TRY(reset_control(h));
-    CocgArgs c{};
-    c.mesh = h->md;
-    c.N = h->N;
-    c.H = h->H;
-    c.inv_dT = 1.0 / h->dT;
-    // FP32 Krylov recurrences cannot resolve FP64-level tolerances; an inexact
-    // coarse solve only slows PP-PC (its fixed point does not depend on it).
-    c.tol = h->coarse_fp32 ? std::max(h->cfg.tol_coarse, kFp32KrylovFloor) : h->cfg.tol_coarse;
-    c.max_it = h->cfg.max_coarse;
-    c.Kbar = h->Kbar;
-    c.tw = h->tw;
-    c.b = h->b;
-    c.x = h->cx;
-    c.r = h->cr;
-    c.z = h->cz;
-    c.w = h->cw;
-    c.p = h->cp;
-    c.s = h->cs;
-    c.invd_sp = h->cinvd;
-    c.part = h->part;
-    c.bar = h->bar;
-    c.status = h->status;
-    c.counters = h->counters;
+    const CocgArgs c = cocg_args(h);
     CK(launch_cocg(c, h->coarse_fp32, h->cocg_cfg, h->st));
     h->stats.launches += 1;
     TRY(device_status(h, "harmonic solves"));
@@ -316,7 +345,7 @@ pppc_status run_ppic_sweep(pppc_handle* h, const double* Ul, const double* Fl, d
     const int lin = h->cfg.coarse_lin;
     CK(cudaEventRecord(h->ev[2], h->st));
     if (lin != PPPC_COARSE_ZERO_FIELD && h->md.n_nl > 0) {
-        launch_elem_data(h->md, h->NB, Ul, h->elem, h->st);
+        launch_elem_data(h->md, h->NB, h->cfg.coarse_at == PPPC_COARSE_AT_F ? Fl : Ul, h->elem, h->st);
         h->stats.launches += 1;
     }
     if (h->md.n_slots > 0) {
@@ -379,18 +408,19 @@ void swap_state(pppc_handle* h) {
 }
 
 pppc_status begin_call(pppc_handle* h) {
-    CK(cudaMemsetAsync(h->counters, 0, 3 * sizeof(long long), h->st));
+    CK(cudaMemsetAsync(h->counters, 0, kCounters * sizeof(long long), h->st));
     h->stats = pppc_stats{};
     return PPPC_OK;
 }
 
 pppc_status end_call(pppc_handle* h) {
-    long long c[3];
+    long long c[kCounters];
     CK(cudaMemcpyAsync(c, h->counters, sizeof c, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     h->stats.newton_iters = c[0];
     h->stats.pcg_iters = c[1];
     h->stats.cocg_iters = c[2];
+    h->stats.backtracks = c[3];
     return PPPC_OK;
 }
 
@@ -440,6 +470,7 @@ void pppc_config_default(pppc_config* c) {
     c->eta0 = 1e-2;
     c->predictor = 1;
     c->method = PPPC_METHOD_PPPC;
+    c->coarse_at = PPPC_COARSE_AT_U;
 }
 
 const char* pppc_status_string(pppc_status s) {
@@ -470,6 +501,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (!(c.tol_newton > 0.0) || !(c.tol_lin > 0.0) || !(c.tol_coarse > 0.0)) why = "tolerances must be positive";
     else if (!(c.eta0 > 0.0) || !(c.eta0 < 1.0)) why = "eta0 must be in (0, 1)";
     else if (c.method != PPPC_METHOD_PPPC && c.method != PPPC_METHOD_PPIC) why = "unknown method";
+    else if (c.coarse_at != PPPC_COARSE_AT_U && c.coarse_at != PPPC_COARSE_AT_F) why = "unknown coarse_at";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
@@ -520,6 +552,8 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
                 !std::isfinite(q.k3))
                 return fail(h, PPPC_ERR_INVALID_ARG,
                             "region " + std::to_string(r) + ": Brauer needs k1 > 0, k2 >= 0, k3 > 0");
+            if (!(q.bmax >= 0.0) || !std::isfinite(q.bmax))
+                return fail(h, PPPC_ERR_INVALID_ARG, "region " + std::to_string(r) + ": bmax must be >= 0");
             kinds[r] |= ELEM_NONLINEAR;
         } else {
             return fail(h, PPPC_ERR_INVALID_ARG, "region " + std::to_string(r) + ": unknown nu_model");
@@ -534,6 +568,7 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         m[4] = q.k2;
         m[5] = q.k3;
         m[6] = q.is_source ? 1.0 : 0.0;
+        m[7] = q.bmax > 0.0 ? q.bmax * q.bmax : INFINITY;   // cap on b = |B|^2
     }
     free_all(h);
     h->has_source = false;
@@ -674,7 +709,7 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     TRY(alloc_n(h, &h->uprev, LV));
     TRY(alloc_n(h, &h->d, LV));
     TRY(alloc_n(h, &h->elem, (size_t)kElemPlanes * hm.n_nl * h->NB));
-    void** fv[] = {&h->r, &h->z, &h->w, &h->p, &h->s, &h->x};
+    void** fv[] = {&h->r, &h->z, &h->w, &h->p, &h->s, &h->x, &h->dx};
     for (void** v : fv) {
         *v = dev_alloc(h, LV * ts);
         if (!*v) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
@@ -703,39 +738,14 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nb, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        std::vector<double> cum(hm.ndof + 1, 0.0);
-        for (int i = 0; i < hm.ndof; ++i) {
-            const int nz = hm.rowptr[i + 1] - hm.rowptr[i];
-            cum[i + 1] = cum[i] + 2.0 + nz * (hm.row_slot[i] >= 0 ? 2.0 : 1.0) + (nz > 32 ? 400.0 : 0.0);
-        }
-        std::vector<int> rs(nb + 1, hm.ndof);
-        rs[0] = 0;
-        int i = 0, rows_max = 0;
-        for (int b = 1; b < nb; ++b) {
-            const double target = cum[hm.ndof] * b / nb;
-            while (i < hm.ndof && cum[i] < target) ++i;
-            rs[b] = i;
-        }
-        for (int b = 0; b < nb; ++b) rows_max = std::max(rows_max, rs[b + 1] - rs[b]);
+        std::vector<int> rs, ls, lrows;
+        int rows_max = 0;
+        partition_rows(hm, nb, rs, ls, lrows, &rows_max);
         TRY(upload(h, &h->d_row_start, rs));
-        std::vector<int> ls(nb + 1, 0), lrows;
-        for (int b = 0; b < nb; ++b) {
-            for (int r = rs[b]; r < rs[b + 1]; ++r)
-                if (hm.rowptr[r + 1] - hm.rowptr[r] > 32) lrows.push_back(r);
-            ls[b + 1] = (int)lrows.size();
-        }
         TRY(upload(h, &h->d_long_start, ls));
         TRY(upload(h, &h->d_long_rows, lrows));
         // keep p, s, x, w in shared memory when a block's rows fit
-        const int V = h->fp32 ? 4 : 2, G = h->NB / V, threads = G * (1024 / G);
-        h->vec_rows = 0;
-        h->vec_w = 0;
-        if (fine_smem(h->fp32, h->NB, threads, rows_max, 4) + 1024 <= (size_t)smem_optin) {
-            h->vec_rows = rows_max;
-            h->vec_w = 1;
-        } else if (fine_smem(h->fp32, h->NB, threads, rows_max, 3) + 1024 <= (size_t)smem_optin) {
-            h->vec_rows = rows_max;
-        }
+        choose_vec_rows(h->fp32, h->NB, rows_max, (size_t)smem_optin - 1024, &h->vec_rows, &h->vec_w);
         CK(fine_config(h->fp32, h->NB, h->vec_rows, h->vec_w ? 4 : 3, &h->fine_cfg));
         if (h->fine_cfg.blocks != nb) return fail(h, PPPC_ERR_CUDA, "fine sweep: one block per SM expected");
     }
@@ -746,7 +756,7 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     TRY(alloc_n(h, &h->part, np));
     TRY(alloc_n(h, &h->jsums, 2));
     TRY(alloc_n(h, &h->bar, 1));
-    TRY(alloc_n(h, &h->counters, 3));
+    TRY(alloc_n(h, &h->counters, kCounters));
     TRY(alloc_n(h, &h->ext, (size_t)h->N * hm.n_nodes));
     CK(cudaMemsetAsync(h->U, 0, LV * sizeof(double), h->st));
     if (h->cfg.method == PPPC_METHOD_PPIC) {
@@ -758,7 +768,7 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         CK(cudaMemsetAsync(h->tw_c1, 0, 2 * sizeof(double), h->st));
         CK(cocg_config(false, 1, &h->cocg1_cfg));
     }
-    CK(cudaMemsetAsync(h->counters, 0, 3 * sizeof(long long), h->st));
+    CK(cudaMemsetAsync(h->counters, 0, kCounters * sizeof(long long), h->st));
     CK(cudaStreamSynchronize(h->st));
     h->has_mesh = true;
     return PPPC_OK;

@@ -51,7 +51,7 @@ struct MeshDev {
     // nonlinear (Brauer) elements
     const int* nl_dofs;    // [n_nl*3] vertex dofs, -1 on the Dirichlet boundary
     const double* nl_geom; // [n_nl*8] area, gx0, gy0, gx1, gy1, gx2, gy2, pad
-    const double* nl_k;    // [n_nl*4] k1, k2, k3, pad
+    const double* nl_k;    // [n_nl*4] k1, k2, k3, cap on |B|^2 (infinite: none)
     const int* nlc_ptr;    // [n_slots+1] nonlinear contributions of each slot
     const int* nlc;        // packed e*9 + a*3 + b  (e: nonlinear element index)
     const double* nlc_ab;  // grad N_a . grad N_b of that element
@@ -81,6 +81,7 @@ struct FineArgs {
     double* elem;            // [5*n_nl*NB]
     void* r; void* z; void* w; void* p; void* s;   // [ndof*NB] of T
     void* x;                 // [ndof*NB] of T: the Newton correction being solved for
+    void* dx;                // [ndof*NB] of T: each lane's last accepted Newton step (for backtracking)
     double eta0;             // PCG forcing term of the first Newton iteration of a step
     int predictor;           // 1: start each step's Newton from 2 u^m - u^{m-1}
     void* J;                 // [n_slots*NB] of T
@@ -93,10 +94,11 @@ struct FineArgs {
     int vec_w;               // 1: w as well
     GridBarrier* bar;
     int* status;
-    long long* counters;     // [0] newton iterations, [1] pcg iterations
+    long long* counters;     // [0] newton tests, [1] pcg iterations, [3] rounds with a backtracking lane
     double* trace;           // optional [trace_cap * kTraceFields] Newton records, or null
     int trace_cap;
     int* trace_len;          // records written (may exceed trace_cap; extra ones dropped)
+    long long* team_ns;      // optional [2]: %globaltimer at the team's start and end
 };
 
 // One record per Newton test of the fine sweep:
@@ -119,6 +121,7 @@ struct CocgArgs {
     GridBarrier* bar;
     int* status;
     long long* counters;     // [2] cocg iterations
+    long long* team_ns;      // optional [2]: %globaltimer at the team's start and end
 };
 
 }  // namespace pppc

@@ -166,8 +166,12 @@ __device__ __forceinline__ void stc(T* p, cplx v) {
 
 constexpr int CNV = 5;  // per lane: |r|^2, (r,z) re/im, (z,w) re/im
 
+// The whole solve for one team of nblk blocks (bid = this block's place in
+// it): the grid of a single-instance launch, or one member's share of a
+// batched launch.  Threads beyond the last whole row group (blockDim not a
+// multiple of H) take no rows.
 template <typename T>
-__global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
+__device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, const int nblk) {
     extern __shared__ double smem[];
     const MeshDev m = a.mesh;
     const int H = a.H;
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
     double* s_tmp = s_sums + CNV * H;      // [blockDim]
     int* s_act = reinterpret_cast<int*>(s_tmp + blockDim.x);
     __shared__ int s_err;
-    double* part_buf[2] = {a.part, a.part + (size_t)gridDim.x * CNV * H};
+    double* part_buf[2] = {a.part, a.part + (size_t)nblk * CNV * H};
     int parity = 0;
 
     T* x = static_cast<T*>(a.x);
@@ -192,12 +196,14 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
     T* p = static_cast<T*>(a.p);
     T* s = static_cast<T*>(a.s);
     T* invd = static_cast<T*>(a.invd_sp);
-    const int rstride = gridDim.x * RB;
-    const int row0 = blockIdx.x * RB + rb;
+    const bool in_group = rb < RB;
+    const int rstride = nblk * RB;
+    const int row0 = in_group ? bid * RB + rb : m.ndof;
     // shift c_p = 1 - z_p of this thread's harmonic
     const cplx cp = {1.0 - a.tw[2 * pl], -a.tw[2 * pl + 1]};
     long long iters = 0;
     if (tid == 0) s_err = 0;
+    if (a.team_ns && bid == 0 && tid == 0) a.team_ns[0] = global_ns();
 
     // init: x = p = s = 0, r = b, z = D^-1 r
     for (int i = row0; i < m.ndof; i += rstride) {
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
         stc<T>(r + o, rv);
         stc<T>(z + o, cmul(iv, rv));
     }
-    if (!grid_sync(a.bar, a.status)) return;
+    if (!grid_sync(a.bar, a.status, bid, nblk)) return;
 
     for (int k = 0;; ++k) {
         double acc[CNV] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -254,17 +260,18 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
             acc[4] += zw.im;
         }
 #pragma unroll
-        for (int q = 0; q < CNV; ++q) s_red[(q * RB + rb) * H + pl] = acc[q];
+        for (int q = 0; q < CNV; ++q)
+            if (in_group) s_red[(q * RB + rb) * H + pl] = acc[q];
         __syncthreads();
-        double* out = part_buf[parity] + (size_t)blockIdx.x * CNV * H;
+        double* out = part_buf[parity] + (size_t)bid * CNV * H;
         for (int o = tid; o < CNV * H; o += blockDim.x) {
             const int q = o / H, l = o - q * H;
             double sum = 0.0;
             for (int t = 0; t < RB; ++t) sum += s_red[(q * RB + t) * H + l];
             out[o] = sum;
         }
-        if (!grid_sync(a.bar, a.status)) return;
-        block_reduce_all<double>(part_buf[parity], CNV * H, s_sums, s_tmp);
+        if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+        block_reduce_all<double>(part_buf[parity], CNV * H, s_sums, s_tmp, nblk);
         parity ^= 1;
 
         int act = 0;
@@ -334,9 +341,32 @@ __global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
             stc<T>(r + o, rv);
             stc<T>(z + o, cmul(iv, rv));
         }
-        if (!grid_sync(a.bar, a.status)) return;
+        if (!grid_sync(a.bar, a.status, bid, nblk)) return;
     }
-    if (blockIdx.x == 0 && tid == 0) a.counters[2] += iters;
+    if (bid == 0 && tid == 0) {
+        a.counters[2] += iters;
+        if (a.team_ns) a.team_ns[1] = global_ns();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
+    cocg_body<T>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched launch of 512-thread blocks: block b serves member map[b].x as
+// block map[b].y of a team of map[b].z blocks (map[b].x < 0: idle).
+template <typename T>
+__global__ void __launch_bounds__(512) cocg_batch_kernel(const CocgArgs* args, const int4* map) {
+    __shared__ CocgArgs s_a;
+    const int4 mb = map[blockIdx.x];
+    if (mb.x < 0) return;
+    static_assert(sizeof(CocgArgs) % sizeof(int) == 0, "CocgArgs copied as words");
+    const int* src = reinterpret_cast<const int*>(args + mb.x);
+    int* dst = reinterpret_cast<int*>(&s_a);
+    for (int q = threadIdx.x; q < (int)(sizeof(CocgArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    cocg_body<T>(s_a, mb.y, mb.z);
 }
 
 size_t cocg_smem(int H, int threads) {
@@ -473,7 +503,7 @@ cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg) {
     const int threads = H * (512 / H);
     const size_t smem = cocg_smem(H, threads);
     const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(fn);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -491,6 +521,31 @@ cudaError_t launch_cocg(const CocgArgs& a, bool fp32, const LaunchCfg& cfg, cuda
     void* args[] = {const_cast<CocgArgs*>(&a)};
     const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
     return cudaLaunchCooperativeKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+size_t cocg_smem_bytes(int H, int threads) { return cocg_smem(H, threads); }
+
+cudaError_t cocg_batch_prepare(size_t* static_smem) {
+    const void* fn = (const void*)cocg_batch_kernel<double>;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (static_smem) *static_smem = fa.sharedSizeBytes;
+    return allow_max_dynamic_smem(fn);
+}
+
+cudaError_t launch_cocg_batch(const CocgArgs* args, const int4* map, int blocks, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cocg_batch_kernel<double>, args, map);
 }
 
 void launch_ppic_start(int ndof, int NB, const double* U, const double* UN, double* dcur, double* Unew,

@@ -12,6 +12,20 @@ namespace pppc {
 // DEV_ERR_TIMEOUT; no phase of any kernel legitimately takes longer.
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
+// Lets kernel fn take all the dynamic shared memory a block may opt into.
+// The limit is a property of the function shared by every handle, so it is
+// set once to the device maximum rather than to one launch's size (a later,
+// smaller setting would make an earlier handle's launches fail).
+inline cudaError_t allow_max_dynamic_smem(const void* fn) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -82,16 +96,18 @@ __device__ __forceinline__ bool spin_until(Pred pred, int* status) {
     return true;
 }
 
-// Grid barrier with one atomic per block: block 0 adds 2^31 - (blocks - 1),
-// every other block adds 1, so the counter grows by exactly 2^31 per round
-// and its top bit flips when the last block arrives; each block waits for
-// that flip relative to the value it saw.  Returns false if the wait timed
-// out here or in another block (the caller then returns).
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
+// Barrier over a team of nblk blocks (the whole grid, or the blocks of one
+// batch member), bid = this block's index in the team, with one atomic per
+// block: block 0 adds 2^31 - (nblk - 1), every other block adds 1, so the
+// counter grows by exactly 2^31 per round and its top bit flips when the last
+// block arrives; each block waits for that flip relative to the value it
+// saw.  Returns false if the wait timed out here or in another block (the
+// caller then returns).
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status, int bid, int nblk) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+        const unsigned int add = bid == 0 ? 0x80000000u - (unsigned int)(nblk - 1) : 1u;
         __threadfence();
         const unsigned int old = atomicAdd(&bar->flip, add);
         int ok = spin_until([&] { return ((ld_acquire_u32(&bar->flip) ^ old) & 0x80000000u) != 0u; }, status);
@@ -102,9 +118,13 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
     __syncthreads();
     return s_ok != 0;
 }
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
+    return grid_sync(bar, status, blockIdx.x, gridDim.x);
+}
 
-// Cross-block reduction without a serial last block.  Every block writes its
-// partial sums block-major, part[b * nvals + o]; after one grid_sync every
+// Cross-block reduction without a serial last block.  Each of the nb blocks
+// of a team writes its partial sums block-major, part[b * nvals + o]; after
+// one grid_sync every
 // block reduces all of them itself, in one fixed order, into shared memory.
 // All blocks therefore hold bitwise-identical sums and take identical
 // decisions.  Thread t sums the partials of output t % nvals over the blocks
@@ -112,8 +132,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
 // chunk results are added in chunk order (tmp[blockDim] holds them).  The caller alternates between two partial buffers so that
 // writing the next partials never overtakes a slower block still reading.
 template <typename RT>
-__device__ __forceinline__ void block_reduce_all(const RT* part, int nvals, RT* sums, RT* tmp) {
-    const int nb = gridDim.x;
+__device__ __forceinline__ void block_reduce_all(const RT* part, int nvals, RT* sums, RT* tmp, int nb) {
     const int t = threadIdx.x;
     if (nvals >= (int)blockDim.x) {  // more values than threads: one thread per value
         for (int o = t; o < nvals; o += blockDim.x) {

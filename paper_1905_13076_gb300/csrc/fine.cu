@@ -39,8 +39,9 @@
 namespace pppc {
 
 // Element data of nonlinear element q, lane `lane`, from the state u:
-//   grad A = sum_a u_a grad N_a,  b = |grad A|^2,
-//   nu = k1 exp(k2 b) + k3,  dnu/db = k1 k2 exp(k2 b),
+//   grad A = sum_a u_a grad N_a,  b = |grad A|^2,  bc = min(b, cap),
+//   nu = k1 exp(k2 bc) (1 + k2 (b - bc)) + k3,  dnu/db = k1 k2 exp(k2 bc)
+//   (the Brauer law, continued past the cap by its tangent in b),
 //   c1 = |e| nu,  c2 = 2 |e| dnu/db,  s_a = grad N_a . grad A.
 __device__ __forceinline__ void elem_compute(const MeshDev& m, int NB, const double* u, double* elem,
                                              int q, int lane) {
@@ -59,8 +60,9 @@ __device__ __forceinline__ void elem_compute(const MeshDev& m, int NB, const dou
     const double gx = d1 * G[3] + d2 * G[5];
     const double gy = d1 * G[4] + d2 * G[6];
     const double b = gx * gx + gy * gy;
-    const double ex = exp(K[1] * b);
-    const double nu = K[0] * ex + K[2];
+    const double bc = fmin(b, K[3]);
+    const double ex = exp(K[1] * bc);
+    const double nu = K[0] * ex * (1.0 + K[1] * (b - bc)) + K[2];
     const double dnu = K[0] * K[1] * ex;
     const size_t P = (size_t)m.n_nl * NB;
     const size_t o = (size_t)q * NB + lane;
@@ -87,6 +89,18 @@ constexpr double kStagnation = 0.5;
 constexpr double kFloorMult = 100.0;
 // Rows with more nonzeros are multiplied by the whole block (see long_rows).
 constexpr int kLongRow = 32;
+// FP32 Jacobian (mixed path): a nonlinear element whose reluctivity exceeds
+// this has its whole Jacobian contribution scaled by kNuCapFp32 / nu, which
+// keeps J symmetric positive definite and the FP32 PCG within range.  The
+// Brauer steel passes it near |B| = 3.2 T, above any converged state of the
+// cable workloads; a cold start at full current can overshoot to ~10 T, where
+// nu exceeds the FP32 range.  The residual stays exact FP64, so converged
+// states do not depend on the cap, and Newton is exact once no element is
+// above it.
+constexpr double kNuCapFp32 = 1e10;
+// Smallest fraction of a Newton step that backtracking tries before the
+// lane reports failure (20 halvings).
+constexpr double kMinStep = 1.0 / 1048576.0;
 
 // V adjacent lanes of one row, loaded and stored as one vector access.
 template <typename T, int V>
@@ -127,13 +141,13 @@ __host__ __device__ inline int red_slots(int G, int threads) {
 }
 
 // Fixed-order in-block reduction over the row groups of each lane, written as
-// this block's partials part[blockIdx.x * NVP * NB + v * NB + lane].  When a
+// this block's partials out[v * NB + lane].  When a
 // warp holds several row groups (G < 32 threads per row) they are first
 // combined with a fixed shuffle tree; the per-warp results are then summed in
 // warp order by one thread per (value, lane).  s_red must hold
 // NVP * (blockDim/32) * NB values (NVP * blockDim/G in the general case).
 template <typename RT, int V, int NVP>
-__device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0, RT (&v)[NVP][V], RT* part) {
+__device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0, RT (&v)[NVP][V], RT* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if (G < 32 && (32 % G) == 0) {
 #pragma unroll
@@ -147,7 +161,6 @@ __device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0,
 #pragma unroll
                 for (int h = 0; h < V; ++h) s_red[(q * nwarps + warp) * NB + l0 + h] = v[q][h];
         __syncthreads();
-        RT* out = part + (size_t)blockIdx.x * NVP * NB;
         for (int o = threadIdx.x; o < NVP * NB; o += blockDim.x) {
             const int q = o / NB, l = o - q * NB;
             RT acc = 0;
@@ -173,7 +186,6 @@ __device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0,
         __syncthreads();
         n = half;
     }
-    RT* out = part + (size_t)blockIdx.x * NVP * NB;
     for (int o = threadIdx.x; o < NVP * NB; o += blockDim.x) {
         const int q = o / NB, l = o - q * NB;
         out[o] = s_red[(q * RB) * NB + l];
@@ -242,6 +254,9 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                             const int pk = m.nlc[c];
                             const int q = pk / 9, ia = (pk / 3) % 3, ib = pk % 3;
                             const double ab = m.nlc_ab[c];
+                            // area * cap: c1 = area * nu above it marks a capped element
+                            const double c1cap = std::is_same<T, float>::value ? kNuCapFp32 * m.nl_geom[8 * (size_t)q]
+                                                                              : 0.0;
                             const size_t eo = (size_t)q * NB + l0;
                             const Lanes<double, V> c1 = ldv<double, V>(E + eo);
                             const Lanes<double, V> c2 = ldv<double, V>(E + P + eo);
@@ -249,7 +264,11 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                             const Lanes<double, V> sb = ldv<double, V>(E + (2 + ib) * P + eo);
 #pragma unroll
                             for (int h = 0; h < V; ++h) {
-                                Jv[h] += c1.v[h] * ab + c2.v[h] * sa.v[h] * sb.v[h];
+                                const double jc = c1.v[h] * ab + c2.v[h] * sa.v[h] * sb.v[h];
+                                if constexpr (std::is_same<T, float>::value)
+                                    Jv[h] += c1.v[h] > c1cap ? jc * (c1cap / c1.v[h]) : jc;
+                                else
+                                    Jv[h] += jc;
                                 if (j == i) acc[h] += c1.v[h] * sa.v[h];
                             }
                         }
@@ -282,8 +301,47 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
             }
 }
 
+// On this thread's rows and lanes: u += x and dx = x for lanes that took a
+// Newton step (coef 1), u += coef * dx for lanes that backtrack (coef < 0),
+// nothing for the others.  Out of line for the same reason as residual_rows.
+template <typename T, int V>
+__device__ __noinline__ void apply_steps(double* u, const T* xB, size_t vo, T* dx, const double* s_coef, int row0,
+                                         int re, int RB, int l0, int NB) {
+    double cf[V];
+    bool step = false, keep = false, back = false;
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+        cf[h] = s_coef[l0 + h];
+        step |= cf[h] == 1.0;
+        keep |= cf[h] != 1.0;
+        back |= cf[h] < 0.0;
+    }
+    if (!step && !back) return;
+    for (int i = row0; i < re; i += RB) {
+        const size_t o = (size_t)i * NB + l0;
+        const Lanes<T, V> xi = ldv<T, V>(xB + (o - vo));
+        Lanes<double, V> ui = ldv<double, V>(u + o);
+        Lanes<T, V> di;
+        if (back || keep) di = ldv<T, V>(dx + o);
+#pragma unroll
+        for (int h = 0; h < V; ++h) {
+            if (cf[h] == 1.0) {
+                ui.v[h] += (double)xi.v[h];
+                di.v[h] = xi.v[h];
+            } else if (cf[h] < 0.0) {
+                ui.v[h] += cf[h] * (double)di.v[h];
+            }
+        }
+        stv<double, V>(u + o, ui);
+        if (step) stv<T, V>(dx + o, di);
+    }
+}
+
+// The whole sweep for one team of nblk blocks (bid = this block's place in
+// it): the grid of a single-instance launch, or one member's share of a
+// batched launch.
 template <typename T>
-__global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
+__device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid, const int nblk) {
     constexpr int V = sizeof(T) == 4 ? 4 : 2;   // lanes per thread: one 16-byte access
     using RT = T;                               // reductions run in the PCG precision
     extern __shared__ double smem[];
@@ -299,13 +357,16 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     double* s_beta = s_alpha + NB;
     double* s_rprev = s_beta + NB; // ||R|| at the previous Newton test
     double* s_eta = s_rprev + NB;  // previous forcing term
-    RT* s_red = reinterpret_cast<RT*>(s_eta + NB);   // [NV][red_slots(G)][NB]
+    double* s_coef = s_eta + NB;   // this round's update u += coef * (x or dx), see below
+    double* s_lam = s_coef + NB;   // fraction of the last Newton step dx now applied
+    RT* s_red = reinterpret_cast<RT*>(s_lam + NB);   // [NV][red_slots(G)][NB]
     RT* s_sums = s_red + NV * red_slots(G, blockDim.x) * NB;  // [NV][NB], identical in every block
     RT* s_tmp = s_sums + NV * NB;                     // [blockDim]
     int* s_newton = reinterpret_cast<int*>(s_tmp + blockDim.x);
     int* s_pcg = s_newton + NB;
+    int* s_nacc = s_pcg + NB;      // accepted Newton steps of the current time step
     __shared__ int s_err;
-    RT* part_buf[2] = {static_cast<RT*>(a.part), static_cast<RT*>(a.part) + (size_t)gridDim.x * NV * NB};
+    RT* part_buf[2] = {static_cast<RT*>(a.part), static_cast<RT*>(a.part) + (size_t)nblk * NV * NB};
     int parity = 0;
 
     // the vectors never alias one another
@@ -325,7 +386,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     const double* E = a.elem;
     const size_t P = (size_t)m.n_nl * NB;
     // this block owns the contiguous rows [rs, re)
-    const int rs = a.row_start[blockIdx.x], re = a.row_start[blockIdx.x + 1];
+    const int rs = a.row_start[bid], re = a.row_start[bid + 1];
     // p, s, x, w are only touched by their owning block: when a.vec_rows > 0
     // they live in shared memory (indexed from row rs), else in global memory
     T* __restrict__ pB = p;
@@ -336,7 +397,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     size_t wo = 0;
     if (a.vec_rows > 0) {
         T* sv = reinterpret_cast<T*>(
-            (reinterpret_cast<uintptr_t>(s_pcg + NB) + 15) & ~static_cast<uintptr_t>(15));
+            (reinterpret_cast<uintptr_t>(s_nacc + NB) + 15) & ~static_cast<uintptr_t>(15));
         const size_t len = (size_t)a.vec_rows * NB;
         pB = sv;
         sB = sv + len;
@@ -350,9 +411,13 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
     }
     const int row0 = rs + rb;
     const long long n_elem_items = (long long)m.n_nl * NB;
-    const long long gthreads = (long long)gridDim.x * blockDim.x;
-    long long newton_total = 0, pcg_total = 0, pcg_since = 0;
+    const long long gthreads = (long long)nblk * blockDim.x;
+    // iteration counts, kept by thread 0: newton tests, pcg iterations, pcg
+    // iterations since the last Newton test, rounds with a backtracking lane
+    __shared__ long long s_cnt[4];
+    if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
     if (tid == 0) s_err = 0;
+    if (a.team_ns && bid == 0 && tid == 0) a.team_ns[0] = global_ns();
 
     for (int step = 0; step < a.n_fine; ++step) {
         for (int l = tid; l < NB; l += blockDim.x) {
@@ -364,6 +429,8 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
             }
             s_I[l] = I;
             s_newton[l] = (l < a.N);
+            s_nacc[l] = 0;
+            s_lam[l] = 1.0;
         }
         // u_prev = u^m on own rows; Newton starts from u^m, or from the linear
         // extrapolation 2 u^m - u^{m-1} once a previous step exists
@@ -380,10 +447,10 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
             }
             stv<double, V>(uprev + o, um);
         }
-        if (extrap && !grid_sync(a.bar, a.status)) return;
-        for (long long it = blockIdx.x * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
+        if (extrap && !grid_sync(a.bar, a.status, bid, nblk)) return;
+        for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
             elem_compute(m, NB, u, a.elem, (int)(it / NB), (int)(it % NB));
-        if (!grid_sync(a.bar, a.status)) return;
+        if (!grid_sync(a.bar, a.status, bid, nblk)) return;
 
         for (int nit = 0;; ++nit) {
             // ---- residual R(u), per-lane Jacobian of special rows, r = -R, z = D^-1 r, x = 0
@@ -403,27 +470,40 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                     v[1][h] = accz[h];
                     v[2][h] = (RT)0;
                 }
-                block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity]);
+                block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity] + (size_t)bid * NV * NB);
             }
-            if (!grid_sync(a.bar, a.status)) return;
-            block_reduce_all<RT>(part_buf[parity], NV * NB, s_sums, s_tmp);
+            if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+            block_reduce_all<RT>(part_buf[parity], NV * NB, s_sums, s_tmp, nblk);
             parity ^= 1;
 
-            // ---- Newton test per lane; PCG forcing term per lane
-            int act = 0;
+            // ---- Newton test per lane; PCG forcing term per lane.  A lane
+            // whose FP64 residual did not drop (or is not finite) after a step
+            // backtracks: the step is halved (u -= lam/2 dx) and tested again.
+            int act = 0, bt = 0;
             for (int l = tid; l < NB; l += blockDim.x) {
                 int al = 0;
+                double coef = 0.0;
                 if (s_newton[l]) {
                     const double rr = (double)s_sums[l];
                     const double Rn = sqrt(rr);
-                    if (!isfinite(Rn)) {
-                        set_status(a.status, DEV_ERR_NAN);
-                        s_err = 1;
-                    } else if (Rn <= a.tol_abs ||
-                               (nit > 0 && Rn <= kFloorMult * a.tol_abs && Rn >= kStagnation * s_rprev[l])) {
+                    const bool fin = isfinite(Rn);
+                    if (fin && (Rn <= a.tol_abs ||
+                                (nit > 0 && Rn <= kFloorMult * a.tol_abs && Rn >= kStagnation * s_rprev[l]))) {
                         // converged, or stalled at the rounding floor just above the tolerance
                         s_newton[l] = 0;
-                    } else if (nit >= a.max_newton) {
+                    } else if (nit > 0 && (!fin || Rn > (1.0 - 1e-4 * s_lam[l]) * s_rprev[l])) {
+                        if (s_lam[l] <= kMinStep) {
+                            set_status(a.status, fin ? DEV_ERR_NEWTON : DEV_ERR_NAN);
+                            s_err = 1;
+                        } else {
+                            coef = -0.5 * s_lam[l];
+                            s_lam[l] *= 0.5;
+                            bt = 1;
+                        }
+                    } else if (!fin) {
+                        set_status(a.status, DEV_ERR_NAN);
+                        s_err = 1;
+                    } else if (s_nacc[l] >= a.max_newton) {
                         set_status(a.status, DEV_ERR_NEWTON);
                         s_err = 1;
                     } else {
@@ -443,14 +523,19 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                         // PCG stops once ||r||_2 (the Newton residual's norm) has dropped by eta
                         s_stop[l] = eta * eta * rr;
                         s_rprev[l] = Rn;
+                        s_lam[l] = 1.0;
+                        s_nacc[l] += 1;
+                        coef = 1.0;
                         al = 1;
                     }
                 }
                 s_pcg[l] = al;
-                act |= al;
+                s_coef[l] = coef;
+                act |= al | bt;
             }
+            if (__syncthreads_or(bt) && tid == 0) ++s_cnt[3];
             const int any_newton = __syncthreads_or(act);
-            if (a.trace && blockIdx.x == 0 && tid == 0) {
+            if (a.trace && bid == 0 && tid == 0) {
                 double rmax = 0.0;
                 int nact = 0;
                 for (int l = 0; l < a.N; ++l) {
@@ -464,13 +549,13 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                     t[1] = nit;
                     t[2] = rmax;
                     t[3] = nact;
-                    t[4] = (double)pcg_since;
+                    t[4] = (double)s_cnt[2];
                 }
             }
-            pcg_since = 0;
+            if (tid == 0) s_cnt[2] = 0;
             if (s_err) return;
             if (!any_newton) break;
-            ++newton_total;
+            if (tid == 0) ++s_cnt[0];
 
             // ---- PCG on J x = -R
             for (int k = 0;; ++k) {
@@ -516,7 +601,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                 }
                 // long rows (e.g. the centre node of a polar mesh): every row group
                 // takes a strided share of the nonzeros, then a fixed-order sum
-                for (int lr = a.long_start[blockIdx.x]; lr < a.long_start[blockIdx.x + 1]; ++lr) {
+                for (int lr = a.long_start[bid]; lr < a.long_start[bid + 1]; ++lr) {
                     const int i = a.long_rows[lr];
                     const int kb = m.rowptr[i], ke = m.rowptr[i + 1], slot0 = m.row_slot[i];
                     T wp[V];
@@ -539,7 +624,7 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                         RT vv[1][V];
 #pragma unroll
                         for (int h = 0; h < V; ++h) vv[0][h] = wp[h];
-                        block_partials<RT, V, 1>(s_red, G, NB, l0, vv, s_tmp - (size_t)blockIdx.x * NB);
+                        block_partials<RT, V, 1>(s_red, G, NB, l0, vv, s_tmp);
                     }
                     __syncthreads();
                     if (rb == 0) {
@@ -570,10 +655,10 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                         v[1][h] = rz[h];
                         v[2][h] = zw[h];
                     }
-                    block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity]);
+                    block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity] + (size_t)bid * NV * NB);
                 }
-                if (!grid_sync(a.bar, a.status)) return;
-                block_reduce_all<RT>(part_buf[parity], NV * NB, s_sums, s_tmp);
+                if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+                block_reduce_all<RT>(part_buf[parity], NV * NB, s_sums, s_tmp, nblk);
                 parity ^= 1;
 
                 int act2 = 0;
@@ -616,8 +701,10 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                 const int any_pcg = __syncthreads_or(act2);
                 if (s_err) return;
                 if (!any_pcg) break;
-                ++pcg_total;
-                ++pcg_since;
+                if (tid == 0) {
+                    ++s_cnt[1];
+                    ++s_cnt[2];
+                }
 
                 T alv[V], bev[V];
 #pragma unroll
@@ -659,27 +746,43 @@ __global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
                     stv<T, V>(z + o, zn);
                     stv<T, V>(xB + ov, xn);
                 }
-                if (!grid_sync(a.bar, a.status)) return;
+                if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             }
-            // ---- u += x on own rows, then element data at the corrected state
-            for (int i = row0; i < re; i += RB) {
-                const size_t o = (size_t)i * NB + l0;
-                const Lanes<T, V> xi = ldv<T, V>(xB + (o - vo));
-                Lanes<double, V> ui = ldv<double, V>(u + o);
-#pragma unroll
-                for (int h = 0; h < V; ++h) ui.v[h] += (double)xi.v[h];
-                stv<double, V>(u + o, ui);
-            }
-            if (!grid_sync(a.bar, a.status)) return;
-            for (long long it = blockIdx.x * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
+            // ---- own rows: apply this round's steps, then element data at the new u
+            apply_steps<T, V>(u, xB, vo, static_cast<T*>(a.dx), s_eta + NB, row0, re, RB, l0, NB);
+            if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+            for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
                 elem_compute(m, NB, u, a.elem, (int)(it / NB), (int)(it % NB));
-            if (!grid_sync(a.bar, a.status)) return;
+            if (!grid_sync(a.bar, a.status, bid, nblk)) return;
         }
     }
-    if (blockIdx.x == 0 && tid == 0) {
-        a.counters[0] += newton_total;
-        a.counters[1] += pcg_total;
+    if (bid == 0 && tid == 0) {
+        a.counters[0] += s_cnt[0];
+        a.counters[1] += s_cnt[1];
+        a.counters[3] += s_cnt[3];
+        if (a.team_ns) a.team_ns[1] = global_ns();
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) fine_sweep_kernel(const FineArgs a) {
+    fine_sweep_body<T>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched launch: block b serves member map[b].x as block map[b].y of a team
+// of map[b].z blocks (map[b].x < 0: idle).  The member's arguments are
+// copied to shared memory once.
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) fine_batch_kernel(const FineArgs* args, const int4* map) {
+    __shared__ FineArgs s_a;
+    const int4 mb = map[blockIdx.x];
+    if (mb.x < 0) return;
+    static_assert(sizeof(FineArgs) % sizeof(int) == 0, "FineArgs copied as words");
+    const int* src = reinterpret_cast<const int*>(args + mb.x);
+    int* dst = reinterpret_cast<int*>(&s_a);
+    for (int q = threadIdx.x; q < (int)(sizeof(FineArgs) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    fine_sweep_body<T>(s_a, mb.y, mb.z);
 }
 
 
@@ -689,8 +792,8 @@ size_t fine_smem(bool fp32, int NB, int threads, int vec_rows, int vec_count) {
     const int V = fp32 ? 4 : 2;
     const int slots = red_slots(NB / V, threads);
     const size_t rt = fp32 ? sizeof(float) : sizeof(double);
-    size_t b = (size_t)8 * NB * sizeof(double) + (size_t)(NV * slots * NB + NV * NB + threads) * rt +
-               2 * NB * sizeof(int);
+    size_t b = (size_t)10 * NB * sizeof(double) + (size_t)(NV * slots * NB + NV * NB + threads) * rt +
+               3 * NB * sizeof(int);
     if (vec_rows > 0) b += 16 + (size_t)vec_count * vec_rows * NB * rt;
     return b;
 }
@@ -702,7 +805,7 @@ cudaError_t fine_config(bool fp32, int NB, int vec_rows, int vec_count, LaunchCf
     const int threads = G * (1024 / G);
     const size_t smem = fine_smem(fp32, NB, threads, vec_rows, vec_count);
     const void* fn = fp32 ? (const void*)fine_sweep_kernel<float> : (const void*)fine_sweep_kernel<double>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(fn);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -720,6 +823,32 @@ cudaError_t launch_fine_sweep(const FineArgs& a, bool fp32, const LaunchCfg& cfg
     void* args[] = {const_cast<FineArgs*>(&a)};
     const void* fn = fp32 ? (const void*)fine_sweep_kernel<float> : (const void*)fine_sweep_kernel<double>;
     return cudaLaunchCooperativeKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+cudaError_t fine_batch_prepare(bool fp32, size_t* static_smem) {
+    const void* fn = fp32 ? (const void*)fine_batch_kernel<float> : (const void*)fine_batch_kernel<double>;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (static_smem) *static_smem = fa.sharedSizeBytes;
+    return allow_max_dynamic_smem(fn);
+}
+
+cudaError_t launch_fine_batch(const FineArgs* args, const int4* map, bool fp32, int blocks, size_t smem,
+                              cudaStream_t st) {
+    // cudaLaunchKernelEx with the cooperative attribute: capturable in a graph
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (fp32) return cudaLaunchKernelEx(&cfg, fine_batch_kernel<float>, args, map);
+    return cudaLaunchKernelEx(&cfg, fine_batch_kernel<double>, args, map);
 }
 
 void launch_elem_data(const MeshDev& m, int NB, const double* u, double* elem, cudaStream_t st) {

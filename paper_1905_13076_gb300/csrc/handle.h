@@ -1,0 +1,93 @@
+// Internal: the handle behind the C ABI and the helpers that the batched
+// driver (batch.cu) shares with the single-instance driver (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pppc.h"
+#include "args.h"
+#include "kernels.h"
+#include "mesh_host.h"
+
+struct pppc_handle {
+    using HostMesh = pppc::HostMesh;
+    using MeshDev = pppc::MeshDev;
+    using GridBarrier = pppc::GridBarrier;
+    using LaunchCfg = pppc::LaunchCfg;
+    using SourceDev = pppc::SourceDev;
+    pppc_config cfg{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    bool has_mesh = false, has_source = false;
+    int N = 0, NB = 0, H = 0;
+    double dt = 0.0, dT = 0.0;
+    bool fp32 = false;
+    HostMesh hm;
+    std::vector<void*> allocs;   // everything allocated for the current mesh
+    MeshDev md{};
+    int* d_node_of_dof = nullptr;
+    int* d_dof_of_node = nullptr;
+    int* d_row_start = nullptr;     // [fine blocks + 1] rows owned by each block of the fine sweep
+    int* d_long_start = nullptr;    // [fine blocks + 1]
+    int* d_long_rows = nullptr;     // rows with more than 32 nonzeros, by owning block
+    int vec_rows = 0;               // > 0: fine-sweep vectors p, s, x kept in shared memory
+    int vec_w = 0;                  // 1: and w
+    // lane vectors [ndof][NB]
+    double *U = nullptr, *Unext = nullptr, *F = nullptr, *uprev = nullptr, *d = nullptr;
+    double* elem = nullptr;
+    void *r = nullptr, *z = nullptr, *w = nullptr, *p = nullptr, *s = nullptr, *x = nullptr, *dx = nullptr,
+         *J = nullptr, *invd = nullptr;
+    // coarse
+    double *y = nullptr, *b = nullptr, *Kbar = nullptr, *tw = nullptr;
+    void *cx = nullptr, *cr = nullptr, *cz = nullptr, *cw = nullptr, *cp = nullptr, *cs = nullptr, *cinvd = nullptr;
+    // reductions and control
+    double *part = nullptr, *jsums = nullptr, *scalars = nullptr;
+    GridBarrier* bar = nullptr;
+    int* status = nullptr;
+    long long* counters = nullptr;
+    double* ext = nullptr;   // [N][n_nodes] staging for host states
+    double* trace = nullptr; // Newton trace of the fine sweep (optional)
+    int* trace_len = nullptr;
+    int trace_cap = 0;
+    LaunchCfg fine_cfg, cocg_cfg, cocg1_cfg;
+    // PP-IC: end-of-period state U_N (and its next value), sweep increment, shift 1 "twiddle"
+    double *UN = nullptr, *UNnext = nullptr, *dcur = nullptr, *tw_c1 = nullptr;
+    bool coarse_fp32 = false;       // the harmonic solves run in FP64 in both precisions
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    SourceDev src{};
+    double gnorm = 0.0, src_area = 0.0;
+    pppc_stats stats{};
+};
+
+namespace pppc {
+namespace detail {
+
+// Device counters of a handle: newton tests, pcg iterations, cocg
+// iterations, fine-sweep rounds in which some lane backtracked.
+constexpr int kCounters = 4;
+
+// Record msg as h's last error and return s.
+pppc_status fail(pppc_handle* h, pppc_status s, const std::string& msg);
+// Synchronise h's stream and map h's device status word to a pppc_status.
+pppc_status device_status(pppc_handle* h, const char* where);
+// Arguments of h's fine sweep writing F into Fout, with h's own row
+// partition (callers may replace the partition fields).
+FineArgs fine_args(pppc_handle* h, double* Fout);
+// Arguments of h's batched harmonic solve (Eq. 13).
+CocgArgs cocg_args(pppc_handle* h);
+// Contiguous row ranges for nb blocks of about equal cost (nonzeros;
+// per-lane rows count double; long rows carry a fixed extra cost): rs[nb+1];
+// the long rows grouped by owning block, ls[nb+1] indexing lrows.
+void partition_rows(const HostMesh& hm, int nb, std::vector<int>& rs, std::vector<int>& ls,
+                    std::vector<int>& lrows, int* rows_max);
+// Estimated cost of one fine sweep of h relative to other handles:
+// partition cost x lanes x fine steps.
+double fine_cost_estimate(const pppc_handle* h);
+// Rows of p, s, x (and w) per block that fit in `budget` bytes of dynamic
+// shared memory next to the fine kernel's scratch (0: none).
+void choose_vec_rows(bool fp32, int NB, int rows_max, size_t budget, int* vec_rows, int* vec_w);
+
+}  // namespace detail
+}  // namespace pppc

@@ -49,6 +49,13 @@ struct LaunchCfg {
 cudaError_t fine_config(bool fp32, int NB, int vec_rows, int vec_count, LaunchCfg* cfg);
 size_t fine_smem(bool fp32, int NB, int threads, int vec_rows, int vec_count);
 cudaError_t launch_fine_sweep(const FineArgs& a, bool fp32, const LaunchCfg& cfg, cudaStream_t st);
+// Batched fine sweep: `blocks` blocks of 1024 threads; args[] and map[blocks]
+// (member, team block, team size, unused) in device memory.
+// fine_batch_prepare lifts the dynamic shared-memory limit to the device
+// maximum and reports the kernel's static shared memory.
+cudaError_t fine_batch_prepare(bool fp32, size_t* static_smem);
+cudaError_t launch_fine_batch(const FineArgs* args, const int4* map, bool fp32, int blocks, size_t smem,
+                              cudaStream_t st);
 // element data (c1, c2, s_a) of the nonlinear elements at the lanes of u
 void launch_elem_data(const MeshDev& m, int NB, const double* u, double* elem, cudaStream_t st);
 
@@ -62,6 +69,11 @@ void launch_coarse_rhs(const MeshDev& m, int N, int NB, int H, double inv_dT, co
                        const double* tw, double* y, double* b, cudaStream_t st);
 cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg);
 cudaError_t launch_cocg(const CocgArgs& a, bool fp32, const LaunchCfg& cfg, cudaStream_t st);
+size_t cocg_smem_bytes(int H, int threads);   // dynamic shared memory of one COCG block
+// Batched FP64 COCG: `blocks` blocks of 512 threads; args[] and map[blocks] as
+// for the batched fine sweep.
+cudaError_t cocg_batch_prepare(size_t* static_smem);
+cudaError_t launch_cocg_batch(const CocgArgs* args, const int4* map, int blocks, size_t smem, cudaStream_t st);
 // PP-IC coarse sweep (Eq. 5): start, right-hand side C v, one step n
 void launch_ppic_start(int ndof, int NB, const double* U, const double* UN, double* dcur, double* Unew,
                        cudaStream_t st);

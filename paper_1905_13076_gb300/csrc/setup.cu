@@ -19,7 +19,7 @@
 namespace pppc {
 namespace {
 
-constexpr int kMatStride = 8;  // sigma, nu_model, nu, k1, k2, k3, is_source, 0
+constexpr int kMatStride = 8;  // sigma, nu_model, nu, k1, k2, k3, is_source, cap on |B|^2
 
 __global__ void geom_kernel(SetupArgs a) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < a.n_tri; e += gridDim.x * blockDim.x) {
@@ -148,7 +148,7 @@ __global__ void nl_tables_kernel(SetupArgs a) {
         a.nl_k[4 * (size_t)q + 0] = m[3];
         a.nl_k[4 * (size_t)q + 1] = m[4];
         a.nl_k[4 * (size_t)q + 2] = m[5];
-        a.nl_k[4 * (size_t)q + 3] = 0.0;
+        a.nl_k[4 * (size_t)q + 3] = m[7];
     }
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.n_nlc; c += stride) {
         const int pk = a.nlc[c];

@@ -24,6 +24,7 @@ class Material:
     nu: float = 0.0
     brauer: tuple | None = None   # (k1, k2, k3) for nu(B^2) = k1 exp(k2 B^2) + k3
     is_source: bool = False
+    bmax: float = 0.0             # Brauer: |B| past which nu continues linearly in B^2 (0: no cap)
 
 
 def _as_host(a, dtype):
@@ -42,7 +43,7 @@ class PPPC:
                  coarse_lin: str = "avg_jacobian", tol_newton: float = 1e-10, max_newton: int = 30,
                  tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
                  max_coarse: int = 20000, eta0: float = 1e-2, predictor: bool = True, method: str = "pppc",
-                 stream=None):
+                 coarse_at: str = "U", stream=None):
         self._lib = _lib.load()
         cfg = pppc_config()
         self._lib.pppc_config_default(ctypes.byref(cfg))
@@ -54,6 +55,7 @@ class PPPC:
         cfg.tol_coarse, cfg.max_coarse = float(tol_coarse), int(max_coarse)
         cfg.eta0, cfg.predictor = float(eta0), int(bool(predictor))
         cfg.method = _lib.METHODS[method]
+        cfg.coarse_at = _lib.COARSE_AT[coarse_at]
         cfg.stream = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
         self.cfg = cfg
         h = ctypes.c_void_p()
@@ -96,6 +98,7 @@ class PPPC:
             if m.brauer is not None:
                 mats[r].nu_model = NU_BRAUER
                 mats[r].k1, mats[r].k2, mats[r].k3 = (float(v) for v in m.brauer)
+                mats[r].bmax = float(m.bmax)
             else:
                 mats[r].nu_model = NU_LINEAR
                 mats[r].nu = float(m.nu)
@@ -215,10 +218,75 @@ def from_problem(problem, **cfg) -> PPPC:
     mats = []
     for r in range(len(problem.sigma)):
         brauer = tuple(problem.brauer[r]) if int(problem.nu_model[r]) == NU_BRAUER else None
+        bmax = float(problem.bmax[r]) if getattr(problem, "bmax", None) is not None else 0.0
         mats.append(Material(sigma=float(problem.sigma[r]), nu=float(problem.nu[r]), brauer=brauer,
-                             is_source=bool(problem.is_source[r])))
+                             is_source=bool(problem.is_source[r]), bmax=bmax))
     s = PPPC(problem.T, problem.N, problem.n_fine, **cfg)
     m = problem.mesh
     s.set_mesh(m.xy, m.tri, m.region, m.dirichlet, mats)
     s.set_source(problem.amp, problem.freq, problem.phase)
     return s
+
+
+class PPPCBatch:
+    """Many independent problems solved together (one team of blocks per
+    member in each cooperative launch, two CUDA graphs per iteration).  The
+    members are ``PPPC`` objects with mesh, source and state set; they keep
+    their own states, so ``member.get_state()`` reads the result."""
+
+    def __init__(self, members, autotune: bool = True):
+        self._lib = _lib.load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        b = ctypes.c_void_p()
+        _lib.check_batch(self._lib.pppc_batch_create(arr, len(self.members), int(bool(autotune)),
+                                                     ctypes.byref(b)), None)
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            self._lib.pppc_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        _lib.check_batch(st, self._b)
+
+    def iterate(self) -> np.ndarray:
+        rr = np.zeros(len(self.members))
+        self._check(self._lib.pppc_batch_iterate(self._b, rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return rr
+
+    def solve_periodic(self, tol: float = 1e-8, kmax: int = 50, raise_on_fail: bool = True):
+        """Returns (iters[count], rel_res[count])."""
+        its = np.zeros(len(self.members), dtype=np.int32)
+        rr = np.zeros(len(self.members))
+        st = self._lib.pppc_batch_solve_periodic(self._b, float(tol), int(kmax),
+                                                 its.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                 rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if raise_on_fail or st != 9:   # PPPC_ERR_NOT_CONVERGED
+            self._check(st)
+        return its, rr
+
+    def teams(self):
+        f = np.zeros(len(self.members), dtype=np.int32)
+        c = np.zeros(len(self.members), dtype=np.int32)
+        self._check(self._lib.pppc_batch_get_teams(self._b, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                   c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return f, c
+
+    def stats(self) -> dict:
+        s = _lib.pppc_batch_stats()
+        self._check(self._lib.pppc_batch_get_stats(self._b, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.pppc_batch_stats._fields_}

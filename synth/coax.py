@@ -33,6 +33,7 @@ RADII = (1.0e-3, 2.0e-3, 2.5e-3, 4.0e-3)  # outer radii of core, insulation, she
 _THICKNESS_HALF_MM = (2, 2, 1, 3)         # region thicknesses in units of 0.5 mm
 REGION_CORE, REGION_INSULATION, REGION_SHEATH, REGION_AIR = 0, 1, 2, 3
 BRAUER_STEEL = (3.8, 2.17, 396.2)         # nu(B^2) = k1 * exp(k2 * B^2) + k3
+BRAUER_BMAX = 3.0                         # |B| [T] past which the fit continues along its tangent
 
 NU_LINEAR, NU_BRAUER = 0, 1
 
@@ -174,6 +175,11 @@ class Problem:
     n_fine: int = 20         # fine implicit-Euler steps per subinterval
     kmax: int = 10
     extra: dict = field(default_factory=dict)
+    bmax: np.ndarray = None  # (4,) |B| [T] past which the Brauer fit continues linearly in B^2 (0: never)
+
+    def __post_init__(self):
+        if self.bmax is None:
+            self.bmax = np.zeros(4)
 
     @property
     def L(self) -> int:
@@ -182,7 +188,8 @@ class Problem:
 
 def make_problem(name: str, nr: int, ntheta: int, N: int, n_fine: int, sigma_sheath: float,
                  amp=(10.0,), freq=(50.0,), phase=None, seed: int = 0, T: float = 0.02,
-                 kmax: int = 10, linear_sheath: bool = False, jitter: float = 0.10) -> Problem:
+                 kmax: int = 10, linear_sheath: bool = False, jitter: float = 0.10,
+                 bmax: float = BRAUER_BMAX) -> Problem:
     mesh = coax_mesh(nr, ntheta, seed=seed, jitter=jitter)
     sigma = np.array([0.0, 0.0, sigma_sheath, 0.0])
     nu_model = np.array([NU_LINEAR, NU_LINEAR, NU_LINEAR if linear_sheath else NU_BRAUER, NU_LINEAR],
@@ -195,9 +202,11 @@ def make_problem(name: str, nr: int, ntheta: int, N: int, n_fine: int, sigma_she
     amp = np.asarray(amp, dtype=np.float64)
     freq = np.asarray(freq, dtype=np.float64)
     phase = np.zeros_like(amp) if phase is None else np.asarray(phase, dtype=np.float64)
+    bm = np.zeros(4)
+    bm[REGION_SHEATH] = bmax
     return Problem(name=name, mesh=mesh, sigma=sigma, nu_model=nu_model, nu=nu, brauer=brauer,
                    is_source=is_source, amp=amp, freq=freq, phase=phase, T=T, N=N,
-                   n_fine=n_fine, kmax=kmax)
+                   n_fine=n_fine, kmax=kmax, bmax=bm)
 
 
 # Workloads by name.  Sizes follow the coax cases the method is exercised on:

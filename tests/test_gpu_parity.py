@@ -245,3 +245,61 @@ def test_device_pointers_and_stream():
             F_dev = s.propagate_fine(torch.from_numpy(U0).cuda())
         torch.cuda.synchronize()
         assert np.array_equal(F_dev.cpu().numpy(), F_host)
+
+
+def test_handles_with_different_meshes_coexist():
+    """The kernels' shared-memory limit is per function: a handle created
+    later with a smaller mesh must not break an earlier, larger one."""
+    big = gpu_solver(workload("small"))
+    small = gpu_solver(workload("tiny"))
+    big.iterate()
+    small.iterate()
+    big.iterate()
+    big.close()
+    small.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+def test_cold_start_at_high_current_backtracks(precision, tol):
+    """40 A switched onto a cable at rest: the first Newton iterates of many
+    steps overshoot into the steep part of the Brauer law and the residual
+    grows, so the GPU lanes backtrack.  Each implicit-Euler step still has one
+    solution, which the oracle's undamped Newton also reaches given enough
+    iterations; the two sweeps must agree."""
+    from synth import make_problem
+
+    prob = make_problem("hot", 20, 40, 16, 10, 5e6, amp=(40.0,))
+    m = FEModel(prob)
+    with gpu_solver(prob, precision=precision) as s:
+        F = s.propagate_fine(np.zeros((prob.N, prob.mesh.n_nodes)))
+        st = s.stats()
+    ref = fine_sweep(m, np.zeros((prob.N, m.ndof)), prob.N, prob.n_fine, prob.T, max_newton=200)
+    assert rel(free(prob, F), ref) < tol
+    assert st["backtracks"] > 0
+
+
+def test_coarse_update_at_fine_results_matches_oracle():
+    """Kbar frozen at the fine results F^k instead of U^k."""
+    prob = workload("small")
+    m = FEModel(prob)
+    rng = np.random.default_rng(3)
+    U = knee_states(prob, 2)
+    F = knee_states(prob, 7) + 1e-6 * rng.standard_normal(U.shape) * (prob.mesh.dirichlet == 0)[None]
+    with gpu_solver(prob, tol_coarse=1e-13, coarse_at="F") as s:
+        Unew, _ = s.coarse_update(U, F)
+    ref = oracle_coarse_update(m, free(prob, U), free(prob, F), prob.N, prob.T, coarse="cyclic", at="F")
+    ref_u = oracle_coarse_update(m, free(prob, U), free(prob, F), prob.N, prob.T, coarse="cyclic", at="U")
+    assert rel(free(prob, Unew), ref) < TOL64
+    assert rel(ref_u, ref) > 1e-6             # the two linearisations do differ here
+
+
+def test_pppc_at_fine_results_matches_oracle():
+    prob = workload("tiny")
+    m = FEModel(prob)
+    with gpu_solver(prob, tol_coarse=1e-12, coarse_at="F") as s:
+        iters, rr = s.solve_periodic(tol=1e-11, kmax=40)
+        U = s.get_state()
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=40, at="F")
+    assert ref.converged and rr <= 1e-11
+    assert abs(iters - ref.iterations) <= 1
+    assert rel(free(prob, U), ref.U) < TOL64

@@ -59,6 +59,47 @@ def test_dnu_matches_difference_quotient(small):
     assert small.nu_brauer(np.array([0.0]), el[:1])[0] == pytest.approx(k1 + k3)
 
 
+def test_brauer_cap_continues_along_the_tangent(small):
+    """Past |B| = bmax the law follows its tangent in b = |B|^2: nu and nu'
+    continuous at the cap, nu linear in b beyond it, unchanged below it."""
+    el = small.nonlinear[:1]
+    k1, k2, k3 = small.k[el[0]]
+    bc = small.b2max[el[0]]
+    assert bc == pytest.approx(9.0)                           # 3 T in the sheath of the workloads
+    nu_c = k1 * math.exp(k2 * bc) + k3
+    d_c = k1 * k2 * math.exp(k2 * bc)
+    eps = 1e-9 * bc
+    lo = small.nu_brauer(np.array([bc - eps]), el)[0]
+    hi = small.nu_brauer(np.array([bc + eps]), el)[0]
+    assert lo == pytest.approx(nu_c, rel=1e-7) and hi == pytest.approx(nu_c, rel=1e-7)
+    assert small.dnu_brauer(np.array([bc - eps]), el)[0] == pytest.approx(d_c, rel=1e-7)
+    assert small.dnu_brauer(np.array([bc + eps, 4 * bc]), el) == pytest.approx([d_c, d_c], rel=1e-12)
+    far = np.array([2 * bc, 10 * bc])
+    assert small.nu_brauer(far, el[[0, 0]]) == pytest.approx(nu_c + d_c * (far - bc), rel=1e-12)
+    b2 = np.array([0.5, 4.0])
+    assert np.allclose(small.nu_brauer(b2, el[[0, 0]]), k1 * np.exp(k2 * b2) + k3, rtol=1e-14)
+    # the difference quotient of nu matches nu' on both sides of the cap
+    h = 1e-6
+    for b in (bc - 0.5, bc + 0.5):
+        fd = (small.nu_brauer(np.array([b + h]), el) - small.nu_brauer(np.array([b - h]), el)) / (2 * h)
+        assert fd[0] == pytest.approx(small.dnu_brauer(np.array([b]), el)[0], rel=1e-6)
+
+
+def test_jacobian_matches_central_differences_above_the_cap(small):
+    """A 4 T field: every sheath element is past the cap."""
+    xy = small.problem.mesh.xy[small.free]
+    r = np.hypot(xy[:, 0], xy[:, 1])
+    u = 4.0 * (RADII[3] - r) * (1.0 + 0.001 * np.random.default_rng(5).standard_normal(r.size))
+    gA = small.grad_A(u, small.nonlinear)
+    assert np.all((gA ** 2).sum(1) > small.b2max[small.nonlinear])
+    v = np.random.default_rng(8).standard_normal(small.ndof) * 1e-6
+    J = small.jacobian_K(u)
+    h = 0.01
+    fd = (small.Ku(u + h * v) - small.Ku(u - h * v)) / (2 * h)
+    assert np.linalg.norm(fd - J @ v) < 1e-8 * np.linalg.norm(fd)
+    assert np.linalg.norm(fd - small.chord_K(u) @ v) > 1e-4 * np.linalg.norm(fd)   # the nu' term is kept
+
+
 def test_matrices_symmetric_and_definite(small):
     u = _field_in_knee(small)
     for A in (small.K_lin, small.M, small.jacobian_K(u)):

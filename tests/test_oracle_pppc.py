@@ -152,6 +152,23 @@ def test_ppic_converges_to_same_fixed_point(tiny):
     assert b.iterations >= a.iterations
 
 
+def test_linearisation_at_fine_results_keeps_the_fixed_point(tiny):
+    """The coarse stiffness may be frozen at U^k or at the fine results F^k:
+    at the fixed point the two coincide, so both iterations must reach the
+    same periodic solution; for a linear material the frozen matrices are
+    equal and so are the whole iterations."""
+    p, m = tiny
+    a = pppc(m, p.N, p.n_fine, p.T, tol=1e-11, kmax=40, at="U")
+    b = pppc(m, p.N, p.n_fine, p.T, tol=1e-11, kmax=40, at="F")
+    assert a.converged and b.converged
+    assert rel(b.U, a.U) < 1e-9
+    lin = workload("tiny", linear_sheath=True)
+    ml = FEModel(lin)
+    c = pppc(ml, lin.N, lin.n_fine, lin.T, tol=1e-30, kmax=3, at="U")
+    d = pppc(ml, lin.N, lin.n_fine, lin.T, tol=1e-30, kmax=3, at="F")
+    assert np.allclose(c.history, d.history, rtol=1e-12, atol=0)
+
+
 def test_jump_of_zero_state_is_the_fine_sweep(tiny):
     p, m = tiny
     U = np.zeros((p.N, m.ndof))
