@@ -283,6 +283,40 @@ const char* pppc_last_error(pppc_handle* h);
 /* Static name of a status code. */
 const char* pppc_status_string(pppc_status s);
 
+/* ---- Periodic adjoint: gradient of the eddy-current loss -------------------
+ * Not in the paper; it reuses its method backwards in time.  For the periodic
+ * state held by the handle (solve it first, e.g. pppc_solve_periodic to
+ * 1e-10 or tighter: the gradient is exact for the discrete periodic solution
+ * the state approximates), with the implicit-Euler scheme of the fine
+ * propagator (dt = T / (N n_fine), L = N n_fine levels, u^0 = u^L), the
+ * period-averaged eddy-current loss is
+ *     P = (1/T) sum_m (u^m - u^{m-1})^T M (u^m - u^{m-1}) / dt      [W/m].
+ * Its gradient with respect to the conductivity and the Brauer constants of
+ * one nonlinear, conducting region r follows from the periodic adjoint
+ *     (M/dt + J_m) lam_m = (M/dt) lam_{m+1} + (2/(T dt)) M (du^m - du^{m+1}),
+ * a linear periodic problem backwards in time, solved by PP-PC with the
+ * multi-harmonic coarse solve (Eq. 4, Eqs. 11-14) run backwards.  Its fine
+ * propagators are the fine sweep's kernel in adjoint mode (each level an
+ * iteratively refined Jacobi-PCG solve), with the Jacobians J_m taken at the
+ * forward trajectory, which one forward fine sweep from the state recomputes
+ * at the start of the call.  Kbar is the forward's.
+ *     dP/dsigma_r = P_r / sigma_r - sum_m lam_m^T (M_r / sigma_r) du^m / dt,
+ *     dP/dk_i     = - sum_m lam_m^T d(K(u^m) u^m)/dk_i.
+ * tol and kmax bound the adjoint PP-PC (rel_res of the adjoint jumps).
+ * Errors: INVALID_ARG (region not nonlinear and conducting, tol <= 0),
+ * STATE (no mesh/source, or the state's rel_res > 1e-6: not periodic),
+ * UNSUPPORTED (PP-IC handle), NOT_CONVERGED, the fine sweep's errors, NOMEM.
+ * The handle's state is unchanged. */
+typedef struct pppc_adjoint_result {
+    double loss;          /* P over all conducting regions [W/m] */
+    double grad[4];       /* dP/d(sigma_r, k1_r, k2_r, k3_r) */
+    int32_t iterations;   /* adjoint PP-PC updates */
+    double rel_res;       /* final adjoint rel_res */
+    double forward_rel_res; /* rel_res of the handle's state */
+} pppc_adjoint_result;
+
+pppc_status pppc_adjoint(pppc_handle* h, int32_t region, double tol, int32_t kmax, pppc_adjoint_result* out);
+
 /* ---- Many independent problems in one launch ------------------------------
  * The paper solves one problem at a time.  A batch runs PP-PC (Eq. 4 with the
  * multi-harmonic coarse solve, Eqs. 11-14) on many independent problems --

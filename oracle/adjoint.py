@@ -125,3 +125,26 @@ def loss_gradient(model, traj, T, region, lam=None):
     for m in range(1, L + 1):
         g_k -= dKu_dk(model, traj[m], region) @ lam[m - 1]
     return P, np.concatenate([[g_s], g_k])
+
+
+def solve_adjoint_by_periods(model, traj, T, tol=1e-13, max_periods=1000):
+    """The same lam_1..lam_L by sweeping the recurrence backwards over whole
+    periods, lam_{L+1} taken from the previous sweep's lam_1, until it
+    repeats (the adjoint counterpart of stepping to periodic steady state;
+    one sparse LU per level, reused by every sweep)."""
+    L = traj.shape[0] - 1
+    dt = T / L
+    Mdt = (model.M / dt).tocsr()
+    g = adjoint_rhs(model, traj, T)
+    lus = [spla.splu((Mdt + model.jacobian_K(traj[m])).tocsc()) for m in range(1, L + 1)]
+    lam_next = np.zeros(model.ndof)
+    lam = np.empty((L, model.ndof))
+    for _ in range(max_periods):
+        x = lam_next
+        for m in range(L, 0, -1):
+            x = lus[m - 1].solve(Mdt @ x + g[m - 1])
+            lam[m - 1] = x
+        if np.linalg.norm(lam[0] - lam_next) <= tol * np.linalg.norm(lam[0]):
+            return lam
+        lam_next = lam[0].copy()
+    raise RuntimeError("adjoint sweeps did not become periodic")

@@ -62,6 +62,11 @@ class pppc_mesh_counts(ctypes.Structure):
                 ("special_entries", c_int64), ("nonlinear_elems", c_int64)]
 
 
+class pppc_adjoint_result(ctypes.Structure):
+    _fields_ = [("loss", c_double), ("grad", c_double * 4), ("iterations", c_int32), ("rel_res", c_double),
+                ("forward_rel_res", c_double)]
+
+
 class pppc_batch_stats(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("retunes", c_int32), ("graph_launches", c_int64),
                 ("kernel_launches", c_int64), ("fine_dof_steps", c_int64), ("fine_ms", c_double),
@@ -94,6 +99,7 @@ SIGNATURES = {
     "pppc_status_string": (c_char_p, [c_int32]),
     "pppc_harmonic_solve_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                               c_void_p, c_void_p, c_double, c_int32, c_void_p, _IPTR]),
+    "pppc_adjoint": (c_int32, [c_void_p, c_int32, c_double, c_int32, POINTER(pppc_adjoint_result)]),
     "pppc_batch_create": (c_int32, [POINTER(c_void_p), c_int32, c_int32, POINTER(c_void_p)]),
     "pppc_batch_destroy": (None, [c_void_p]),
     "pppc_batch_iterate": (c_int32, [c_void_p, _DPTR]),

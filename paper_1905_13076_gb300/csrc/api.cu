@@ -307,18 +307,24 @@ pppc_status run_jumps(pppc_handle* h, const double* Ul, const double* Fl, double
     return PPPC_OK;
 }
 
-// Unew = coarse-corrected state from Ul, Fl and the jumps in h->d.
-pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl, double* Unew) {
+// Kbar frozen at the N lanes of `state`.
+pppc_status run_kbar(pppc_handle* h, const double* state) {
     const int lin = h->cfg.coarse_lin;
-    CK(cudaEventRecord(h->ev[2], h->st));
     if (lin != PPPC_COARSE_ZERO_FIELD && h->md.n_nl > 0) {
-        launch_elem_data(h->md, h->NB, h->cfg.coarse_at == PPPC_COARSE_AT_F ? Fl : Ul, h->elem, h->st);
+        launch_elem_data(h->md, h->NB, state, h->elem, h->st);
         h->stats.launches += 1;
     }
     if (h->md.n_slots > 0) {
         launch_kbar(h->md, h->N, h->NB, lin, h->elem, h->Kbar, h->st);
         h->stats.launches += 1;
     }
+    CK(cudaGetLastError());
+    return PPPC_OK;
+}
+
+// Unew = Fl (shifted) + the harmonic correction from the jumps in h->d and
+// the current Kbar (Eqs. 11-14 in delta form).
+pppc_status run_correct(pppc_handle* h, const double* Fl, double* Unew) {
     if (h->md.n_sp > 0) {
         launch_coarse_rhs(h->md, h->N, h->NB, h->H, 1.0 / h->dT, h->d, h->tw, h->y, h->b, h->st);
         h->stats.launches += 2;
@@ -332,6 +338,14 @@ pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl,
     launch_idft_update(h->hm.ndof, h->N, h->NB, h->H, h->coarse_fp32, h->cx, Fl, h->tw, Unew, h->st);
     h->stats.launches += 1;
     CK(cudaGetLastError());
+    return PPPC_OK;
+}
+
+// Unew = coarse-corrected state from Ul, Fl and the jumps in h->d.
+pppc_status run_coarse_solve(pppc_handle* h, const double* Ul, const double* Fl, double* Unew) {
+    CK(cudaEventRecord(h->ev[2], h->st));
+    TRY(run_kbar(h, h->cfg.coarse_at == PPPC_COARSE_AT_F ? Fl : Ul));
+    TRY(run_correct(h, Fl, Unew));
     CK(cudaEventRecord(h->ev[3], h->st));
     CK(cudaEventSynchronize(h->ev[3]));
     float ms = 0.f;
@@ -449,6 +463,17 @@ pppc_status stage_out(pppc_handle* h, const double* lanes, double* U, int on_dev
 }
 
 }  // namespace
+
+// Stages of one iteration, for the adjoint driver (adjoint.cu).
+pppc_status pppc::detail::stage_ready(pppc_handle* h) { return need_ready(h); }
+pppc_status pppc::detail::stage_reset(pppc_handle* h) { return reset_control(h); }
+pppc_status pppc::detail::stage_jumps(pppc_handle* h, const double* Ul, const double* Fl, double* rr) {
+    return run_jumps(h, Ul, Fl, rr);
+}
+pppc_status pppc::detail::stage_kbar(pppc_handle* h, const double* state) { return run_kbar(h, state); }
+pppc_status pppc::detail::stage_correct(pppc_handle* h, const double* Fl, double* Unew) {
+    return run_correct(h, Fl, Unew);
+}
 
 // ===========================================================================
 extern "C" {
@@ -579,6 +604,13 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     if (!build_host_mesh(n_nodes, n_tri, tri, region, dirichlet, n_regions, kinds.data(), h->hm, err))
         return fail(h, PPPC_ERR_INVALID_ARG, err);
     HostMesh& hm = h->hm;
+    h->traj = h->lam = h->adjA = h->adjB = h->adjF = h->gpart = h->gout = nullptr;
+    h->nl_sel = nullptr;
+    h->nl_region.resize(hm.n_nl);
+    for (int q = 0; q < hm.n_nl; ++q) h->nl_region[q] = region[hm.nl_elems[q]];
+    h->region_sigma.resize(n_regions);
+    h->region_kind = kinds;
+    for (int r = 0; r < n_regions; ++r) h->region_sigma[r] = mat[r].sigma;
     bool any_source = false;
     for (int e = 0; e < n_tri && !any_source; ++e) any_source = (hm.elem_kind[e] & ELEM_SOURCE) != 0;
     if (!any_source) return fail(h, PPPC_ERR_INVALID_ARG, "no triangle lies in a source region");

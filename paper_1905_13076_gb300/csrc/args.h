@@ -99,6 +99,13 @@ struct FineArgs {
     int trace_cap;
     int* trace_len;          // records written (may exceed trace_cap; extra ones dropped)
     long long* team_ns;      // optional [2]: %globaltimer at the team's start and end
+    // forward: optional record of every fine level; adjoint mode (see fine.cu)
+    double* traj_out;        // forward: [n_fine+1][ndof][NB] u at levels 0..n_fine of each lane, or null
+    int adjoint;             // 1: each lane runs its subinterval's periodic adjoint backwards
+    const double* traj;      // adjoint: the forward trajectory, layout of traj_out
+    double* lam_out;         // adjoint: [n_fine][ndof][NB] lambda at levels 1..n_fine, or null
+    double tol_rel;          // adjoint: a level is solved when ||R|| <= tol_rel ||b||
+    double g_scale;          // adjoint: 2 / (T dt), the loss weight of the adjoint source
 };
 
 // One record per Newton test of the fine sweep:

@@ -301,6 +301,138 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
             }
 }
 
+// Periodic adjoint (backwards in time) on this thread's rows and lanes at
+// level j of each lane's subinterval (global step m = lane * n_fine + j):
+//   R(lam) = (M/dt)(lam - lam_next) + J_m lam - g_m,
+//   g_m = g_scale M (du^m - du^{m+1}),   du^m = u^m - u^{m-1},
+// J_m = d(K(u)u)/du at the forward state u^m (element data in a.elem were
+// computed from it), lam in a.u, lam_next = lam_{m+1} in a.uprev; at j =
+// n_fine, du^{m+1} is the next lane's first step.  Writes the per-lane
+// Jacobian values of the special rows, r = -R, z = D^-1 r, x = 0, and
+// accumulates sum R^2, (r,z) and sum b^2 of the right-hand side
+// b = (M/dt) lam_next + g_m.  Out of line like residual_rows.
+template <typename T, int V>
+__device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, int row0, int re, int RB, int l0, int j,
+                                          double* accR, T* accz, double* accb, T* xB, size_t vo) {
+    const int NB = a.NB, N = a.N;
+    const size_t P = (size_t)m.n_nl * NB;
+    const size_t lv = (size_t)m.ndof * NB;
+    const double* lam = a.u;
+    const double* lnext = a.uprev;
+    const double* E = a.elem;
+    const double* um = a.traj + (size_t)j * lv;
+    const double* ump = um - lv;
+    const bool last = j == a.n_fine;   // du^{m+1} from the next lane's levels 0, 1
+    T* r = static_cast<T*>(a.r);
+    T* z = static_cast<T*>(a.z);
+    T* J = static_cast<T*>(a.J);
+    T* invd = static_cast<T*>(a.invd_sp);
+    const T* invdiag_linT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.invdiag_lin32)
+                                                          : reinterpret_cast<const T*>(m.invdiag_lin);
+    for (int i = row0; i < re; i += RB) {
+        const int kb = m.rowptr[i], ke = m.rowptr[i + 1];
+        const int slot0 = m.row_slot[i];
+        const size_t o = (size_t)i * NB + l0;
+        double acc[V], bb[V];
+#pragma unroll
+        for (int h = 0; h < V; ++h) acc[h] = bb[h] = 0.0;
+        Lanes<T, V> iv;
+        if (slot0 < 0) {
+            for (int k = kb; k < ke; ++k) {
+                const double kv = m.Klin[k];
+                const Lanes<double, V> lj = ldv<double, V>(lam + (size_t)m.col[k] * NB + l0);
+#pragma unroll
+                for (int h = 0; h < V; ++h) acc[h] += kv * lj.v[h];
+            }
+            const T d = invdiag_linT[i];
+#pragma unroll
+            for (int h = 0; h < V; ++h) iv.v[h] = d;
+        } else {
+            double dg[V];
+            for (int k = kb; k < ke; ++k) {
+                const int sl = slot0 + (k - kb);
+                const int jc = m.col[k];
+                const size_t oc = (size_t)jc * NB + l0;
+                const double kv = m.Klin[k];
+                const double ms = m.Mslot[sl];
+                const double mv = ms * a.inv_dt;
+                const Lanes<double, V> lj = ldv<double, V>(lam + oc);
+                const Lanes<double, V> lnj = ldv<double, V>(lnext + oc);
+                double dd[V];   // du^m - du^{m+1} at node jc
+                if (ms != 0.0) {
+                    const Lanes<double, V> u0 = ldv<double, V>(um + oc);
+                    const Lanes<double, V> u1 = ldv<double, V>(ump + oc);
+                    if (!last) {
+                        const Lanes<double, V> u2 = ldv<double, V>(um + lv + oc);
+#pragma unroll
+                        for (int h = 0; h < V; ++h) dd[h] = (u0.v[h] - u1.v[h]) - (u2.v[h] - u0.v[h]);
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < V; ++h) {
+                            const int ln = (l0 + h + 1) % N;
+                            const size_t on = (size_t)jc * NB + ln;
+                            dd[h] = (u0.v[h] - u1.v[h]) - (a.traj[lv + on] - a.traj[on]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < V; ++h) dd[h] = 0.0;
+                }
+                double Jv[V];
+#pragma unroll
+                for (int h = 0; h < V; ++h) Jv[h] = kv + mv;
+                for (int c = m.nlc_ptr[sl]; c < m.nlc_ptr[sl + 1]; ++c) {
+                    const int pk = m.nlc[c];
+                    const int q = pk / 9, ia = (pk / 3) % 3, ib = pk % 3;
+                    const double ab = m.nlc_ab[c];
+                    const double c1cap = std::is_same<T, float>::value ? kNuCapFp32 * m.nl_geom[8 * (size_t)q] : 0.0;
+                    const size_t eo = (size_t)q * NB + l0;
+                    const Lanes<double, V> c1 = ldv<double, V>(E + eo);
+                    const Lanes<double, V> c2 = ldv<double, V>(E + P + eo);
+                    const Lanes<double, V> sa = ldv<double, V>(E + (2 + ia) * P + eo);
+                    const Lanes<double, V> sb = ldv<double, V>(E + (2 + ib) * P + eo);
+#pragma unroll
+                    for (int h = 0; h < V; ++h) {
+                        const double jc2 = c1.v[h] * ab + c2.v[h] * sa.v[h] * sb.v[h];
+                        if constexpr (std::is_same<T, float>::value)
+                            Jv[h] += c1.v[h] > c1cap ? jc2 * (c1cap / c1.v[h]) : jc2;
+                        else
+                            Jv[h] += jc2;
+                    }
+                }
+                Lanes<T, V> jt;
+#pragma unroll
+                for (int h = 0; h < V; ++h) {
+                    const double rhs = mv * lnj.v[h] + a.g_scale * ms * dd[h];
+                    acc[h] += Jv[h] * lj.v[h] - rhs;
+                    bb[h] += rhs;
+                    jt.v[h] = (T)Jv[h];
+                }
+                stv<T, V>(J + (size_t)sl * NB + l0, jt);
+                if (jc == i)
+#pragma unroll
+                    for (int h = 0; h < V; ++h) dg[h] = Jv[h];
+            }
+#pragma unroll
+            for (int h = 0; h < V; ++h) iv.v[h] = (T)(1.0 / dg[h]);
+            stv<T, V>(invd + (size_t)m.sp_index[i] * NB + l0, iv);
+        }
+        Lanes<T, V> rv, zv, zero;
+#pragma unroll
+        for (int h = 0; h < V; ++h) {
+            rv.v[h] = (T)(-acc[h]);
+            zv.v[h] = rv.v[h] * iv.v[h];
+            zero.v[h] = (T)0;
+            accR[h] += acc[h] * acc[h];
+            accz[h] += rv.v[h] * zv.v[h];
+            accb[h] += bb[h] * bb[h];
+        }
+        stv<T, V>(r + o, rv);
+        stv<T, V>(z + o, zv);
+        stv<T, V>(xB + (o - vo), zero);
+    }
+}
+
 // On this thread's rows and lanes: u += x and dx = x for lanes that took a
 // Newton step (coef 1), u += coef * dx for lanes that backtrack (coef < 0),
 // nothing for the others.  Out of line for the same reason as residual_rows.
@@ -433,11 +565,14 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
             s_lam[l] = 1.0;
         }
         // u_prev = u^m on own rows; Newton starts from u^m, or from the linear
-        // extrapolation 2 u^m - u^{m-1} once a previous step exists
-        const bool extrap = a.predictor && step > 0;
+        // extrapolation 2 u^m - u^{m-1} once a previous step exists.  In the
+        // adjoint, u is lambda, u_prev = lambda_{m+1}, and level j counts down.
+        const int j = a.adjoint ? a.n_fine - step : step;
+        const bool extrap = !a.adjoint && a.predictor && step > 0;
         for (int i = row0; i < re; i += RB) {
             const size_t o = (size_t)i * NB + l0;
             const Lanes<double, V> um = ldv<double, V>(u + o);
+            if (a.traj_out && step == 0) stv<double, V>(a.traj_out + o, um);
             if (extrap) {
                 const Lanes<double, V> uo = ldv<double, V>(uprev + o);
                 Lanes<double, V> un;
@@ -448,27 +583,35 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
             stv<double, V>(uprev + o, um);
         }
         if (extrap && !grid_sync(a.bar, a.status, bid, nblk)) return;
-        for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
-            elem_compute(m, NB, u, a.elem, (int)(it / NB), (int)(it % NB));
+        {
+            // element data of the state the Jacobian is taken at: the Newton
+            // iterate, or in the adjoint the forward state u^m (fixed for the level)
+            const double* eu = a.adjoint ? a.traj + (size_t)j * m.ndof * NB : u;
+            for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
+                elem_compute(m, NB, eu, a.elem, (int)(it / NB), (int)(it % NB));
+        }
         if (!grid_sync(a.bar, a.status, bid, nblk)) return;
 
         for (int nit = 0;; ++nit) {
             // ---- residual R(u), per-lane Jacobian of special rows, r = -R, z = D^-1 r, x = 0
-            double accR[V];
+            double accR[V], accb[V];
             T accz[V];
 #pragma unroll
             for (int h = 0; h < V; ++h) {
-                accR[h] = 0.0;
+                accR[h] = accb[h] = 0.0;
                 accz[h] = 0;
             }
-            residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo);
+            if (a.adjoint)
+                adjoint_rows<T, V>(a, m, row0, re, RB, l0, j, accR, accz, accb, xB, vo);
+            else
+                residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo);
             {
                 RT v[NV][V];
 #pragma unroll
                 for (int h = 0; h < V; ++h) {
                     v[0][h] = (RT)accR[h];
                     v[1][h] = accz[h];
-                    v[2][h] = (RT)0;
+                    v[2][h] = (RT)accb[h];
                 }
                 block_partials<RT, V, NV>(s_red, G, NB, l0, v, part_buf[parity] + (size_t)bid * NV * NB);
             }
@@ -487,8 +630,9 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     const double rr = (double)s_sums[l];
                     const double Rn = sqrt(rr);
                     const bool fin = isfinite(Rn);
-                    if (fin && (Rn <= a.tol_abs ||
-                                (nit > 0 && Rn <= kFloorMult * a.tol_abs && Rn >= kStagnation * s_rprev[l]))) {
+                    // the adjoint's residual is linear: its tolerance is relative to ||b||
+                    const double tol = a.adjoint ? a.tol_rel * sqrt((double)s_sums[2 * NB + l]) : a.tol_abs;
+                    if (fin && (Rn <= tol || (nit > 0 && Rn <= kFloorMult * tol && Rn >= kStagnation * s_rprev[l]))) {
                         // converged, or stalled at the rounding floor just above the tolerance
                         s_newton[l] = 0;
                     } else if (nit > 0 && (!fin || Rn > (1.0 - 1e-4 * s_lam[l]) * s_rprev[l])) {
@@ -518,7 +662,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                             if (safe > 0.1) eta = fmax(eta, safe);
                         }
                         eta = fmin(fmax(eta, a.tol_lin), 0.1);
-                        eta = fmax(eta, fmin(0.1, 0.1 * a.tol_abs / Rn));
+                        eta = fmax(eta, fmin(0.1, 0.1 * tol / Rn));
                         s_eta[l] = eta;
                         // PCG stops once ||r||_2 (the Newton residual's norm) has dropped by eta
                         s_stop[l] = eta * eta * rr;
@@ -751,10 +895,20 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
             // ---- own rows: apply this round's steps, then element data at the new u
             apply_steps<T, V>(u, xB, vo, static_cast<T*>(a.dx), s_eta + NB, row0, re, RB, l0, NB);
             if (!grid_sync(a.bar, a.status, bid, nblk)) return;
-            for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
-                elem_compute(m, NB, u, a.elem, (int)(it / NB), (int)(it % NB));
-            if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+            if (!a.adjoint) {
+                for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
+                    elem_compute(m, NB, u, a.elem, (int)(it / NB), (int)(it % NB));
+                if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+            }
         }
+        // ---- record the level just solved (own rows)
+        double* rec = a.adjoint ? (a.lam_out ? a.lam_out + (size_t)(j - 1) * m.ndof * NB : nullptr)
+                                : (a.traj_out ? a.traj_out + (size_t)(step + 1) * m.ndof * NB : nullptr);
+        if (rec)
+            for (int i = row0; i < re; i += RB) {
+                const size_t o = (size_t)i * NB + l0;
+                stv<double, V>(rec + o, ldv<double, V>(u + o));
+            }
     }
     if (bid == 0 && tid == 0) {
         a.counters[0] += s_cnt[0];

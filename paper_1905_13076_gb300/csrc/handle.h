@@ -59,6 +59,14 @@ struct pppc_handle {
     SourceDev src{};
     double gnorm = 0.0, src_area = 0.0;
     pppc_stats stats{};
+    // per nonlinear element: its region; per region: sigma (for the adjoint)
+    std::vector<int> nl_region;
+    std::vector<double> region_sigma;
+    std::vector<int> region_kind;
+    // adjoint workspace (allocated at the first pppc_adjoint)
+    double *traj = nullptr, *lam = nullptr, *adjA = nullptr, *adjB = nullptr, *adjF = nullptr;
+    double *gpart = nullptr, *gout = nullptr;
+    unsigned char* nl_sel = nullptr;
 };
 
 namespace pppc {
@@ -77,6 +85,14 @@ pppc_status device_status(pppc_handle* h, const char* where);
 FineArgs fine_args(pppc_handle* h, double* Fout);
 // Arguments of h's batched harmonic solve (Eq. 13).
 CocgArgs cocg_args(pppc_handle* h);
+// Stages of one iteration on h's stream: mesh and source present; control
+// words reset; jumps d = F - U into h->d with rel_res; Kbar frozen at the
+// lanes of `state`; harmonic correction Unew = F (shifted) + IDFT(W).
+pppc_status stage_ready(pppc_handle* h);
+pppc_status stage_reset(pppc_handle* h);
+pppc_status stage_jumps(pppc_handle* h, const double* Ul, const double* Fl, double* rel_res);
+pppc_status stage_kbar(pppc_handle* h, const double* state);
+pppc_status stage_correct(pppc_handle* h, const double* Fl, double* Unew);
 // Contiguous row ranges for nb blocks of about equal cost (nonzeros;
 // per-lane rows count double; long rows carry a fixed extra cost): rs[nb+1];
 // the long rows grouped by owning block, ls[nb+1] indexing lrows.

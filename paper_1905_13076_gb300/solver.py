@@ -211,6 +211,15 @@ class PPPC:
         self._check(self._lib.pppc_get_stats(self._h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in pppc_stats._fields_}
 
+    def adjoint(self, region: int, tol: float = 1e-10, kmax: int = 60):
+        """Loss P [W/m] of the current (periodic) state and dP/d(sigma, k1, k2,
+        k3) of region ``region`` by the periodic adjoint.  Returns
+        (loss, grad[4], info)."""
+        r = _lib.pppc_adjoint_result()
+        self._check(self._lib.pppc_adjoint(self._h, int(region), float(tol), int(kmax), ctypes.byref(r)))
+        info = {"iterations": r.iterations, "rel_res": r.rel_res, "forward_rel_res": r.forward_rel_res}
+        return r.loss, np.array(list(r.grad)), info
+
 
 def from_problem(problem, **cfg) -> PPPC:
     """Build a solver from any object shaped like ``synth.coax.Problem``

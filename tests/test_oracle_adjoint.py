@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from oracle.adjoint import adjoint_rhs, eddy_loss, loss_gradient, solve_adjoint
+from oracle.adjoint import adjoint_rhs, eddy_loss, loss_gradient, solve_adjoint, solve_adjoint_by_periods
 from oracle.fem import FEModel
 from oracle.periodic import bruteforce_periodic
 from synth import REGION_SHEATH, make_problem, workload
@@ -93,3 +93,11 @@ def test_loss_is_the_discrete_eddy_power():
     assert P == pytest.approx(tot / (prob.T * dt), rel=1e-12)
     m2 = FEModel(scaled(prob, 0, 2.0))
     assert eddy_loss(m2, traj, prob.T) == pytest.approx(2 * P, rel=1e-12)
+
+
+def test_adjoint_by_periods_matches_direct_solve():
+    prob = workload("tiny")
+    m, traj = periodic(prob)
+    a = solve_adjoint(m, traj, prob.T)
+    b = solve_adjoint_by_periods(m, traj, prob.T)
+    assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
