@@ -51,6 +51,8 @@ def parse():
                     help="instead of the benchmark: PP-PC vs PP-IC iterations to 1e-6 on the paper-shaped case")
     ap.add_argument("--batched", action="store_true",
                     help="instead of the medium benchmark: 32 uneven cables in one batch (two graphs per iteration)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="instead of the medium benchmark: periodic solve + adjoint gradient on the adjoint workload")
     ap.add_argument("--batched-tts", action="store_true",
                     help="with --batched: also solve all 32 cables from rest to rel res 1e-8")
     return ap.parse_args()
@@ -99,6 +101,54 @@ def compare_methods(args, local):
     out["rel_diff_pppc_ppic"] = float(np.linalg.norm(states["pppc"] - states["ppic"])
                                       / np.linalg.norm(states["pppc"]))
     print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args, local):
+    """The adjoint workload: coax nr=160 x ntheta=320 (50 881 unknowns), N =
+    128, 40 fine steps, sheath sigma 2e7.  Periodic solve from rest to rel res
+    1e-10, then the loss and dP/d(sigma, k1, k2, k3) of the sheath by the
+    periodic adjoint to rel res 1e-10 (device times from the library's
+    events; the adjoint's includes the forward trajectory sweep)."""
+    import torch
+
+    from paper_1905_13076_gb300 import from_problem
+    from synth import REGION_SHEATH, workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prob = workload("adjoint")
+    s = from_problem(prob, precision=args.precision, stream=stream)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        its, rr = s.solve_periodic(tol=1e-10, kmax=80, raise_on_fail=False)
+        t_fwd_host = time.perf_counter() - t0
+        fst = s.stats()
+        t0 = time.perf_counter()
+        loss, grad, info = s.adjoint(REGION_SHEATH, tol=1e-10, kmax=80)
+        t_adj_host = time.perf_counter() - t0
+        ast = s.stats()
+    units = prob.N * prob.n_fine * s.ndof
+    fwd_s = (fst["fine_ms"] + fst["coarse_ms"]) * 1e-3
+    adj_s = (ast["fine_ms"] + ast["coarse_ms"]) * 1e-3
+    adj_sweeps = info["iterations"] + 1
+    line = {
+        "metric": "s to periodic steady state and adjoint gradient", "value": fwd_s + adj_s, "unit": "s",
+        "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "coax adjoint case: nr=160 x ntheta=320 (50881 DOFs), N=128, 40 fine steps, "
+                               "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision},
+        "forward": {"seconds": fwd_s, "host_seconds": t_fwd_host, "pppc_iterations": its, "rel_res": rr,
+                    "fine_dof_steps_per_s": units * (its + 1) / (fst["fine_ms"] * 1e-3)},
+        "adjoint": {"seconds": adj_s, "host_seconds": t_adj_host, "pppc_iterations": info["iterations"],
+                    "rel_res": info["rel_res"], "forward_rel_res": info["forward_rel_res"],
+                    "refinement_passes": ast["newton_iters"], "pcg_iters": ast["pcg_iters"],
+                    "fine_dof_steps_per_s": units * (adj_sweeps + 1) / (ast["fine_ms"] * 1e-3)},
+        "loss_w_per_m": loss, "grad": {"sigma": grad[0], "k1": grad[1], "k2": grad[2], "k3": grad[3]},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
 
 
 def run_batched(args, local):
@@ -383,6 +433,10 @@ def main():
     if args.batched:
         if rank == 0:
             run_batched(args, local)
+        return
+    if args.adjoint:
+        if rank == 0:
+            run_adjoint(args, local)
         return
     import numpy as np
     import torch
