@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--newton-schedule", type=int, default=0, choices=[0, 1],
+                    help="timed steps: 1 = inexact PP-PC (fine Newton tolerance tied to the previous rel res)")
+    ap.add_argument("--tts-schedule", type=int, default=1, choices=[0, 1],
+                    help="time-to-steady-state run: 1 = inexact PP-PC (same fixed point, final iterates at the "
+                         "full Newton tolerance)")
     ap.add_argument("--coarse-at", default="U", choices=["U", "F"],
                     help="freeze the coarse stiffness at U^k or at the fine results F^k")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady-state run")
@@ -449,7 +454,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     prob = workload(WORKLOAD)
     mixed = args.precision == "mixed"
-    solver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at, stream=stream)
+    solver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
+                          newton_schedule=bool(args.newton_schedule), stream=stream)
     ndof = solver.ndof
     units_per_step = prob.N * prob.n_fine * ndof
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -525,18 +531,22 @@ def main():
     # ---- time to periodic steady state from U = 0
     tts = None
     if not args.no_tts:
-        solver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
+        tsolver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
+                               newton_schedule=bool(args.tts_schedule), stream=stream)
+        tsolver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         e0.record(stream)
-        iters, rr = solver.solve_periodic(tol=1e-8, kmax=60, raise_on_fail=False)
+        iters, rr = tsolver.solve_periodic(tol=1e-8, kmax=60, raise_on_fail=False)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        st = solver.stats()
+        st = tsolver.stats()
         tts = {"seconds": e0.elapsed_time(e1) * 1e-3, "host_seconds": time.perf_counter() - t0,
                "pppc_iterations": iters, "rel_res": rr, "newton_iters": st["newton_iters"],
-               "pcg_iters": st["pcg_iters"], "cocg_iters": st["cocg_iters"]}
+               "pcg_iters": st["pcg_iters"], "cocg_iters": st["cocg_iters"],
+               "newton_schedule": args.tts_schedule}
+        tsolver.close()
 
     if rank != 0:
         solver.close()
@@ -552,7 +562,7 @@ def main():
         "config": {"workload": "coax medium: nr=100 x ntheta=200 (19801 DOFs), N=64, 50 fine steps, "
                                "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
                    "parallelism": "replicas only", "l2": "flushed between steps (512 MB write)",
-                   "coarse_at": args.coarse_at},
+                   "coarse_at": args.coarse_at, "newton_schedule": args.newton_schedule},
         "time_to_steady_state": tts,
         "per_step": {"pcg_iters": pcg / args.steps, "newton_iters": newton / args.steps,
                      "fine_ms": sum(fine_ms) / args.steps, "step_ms": step_ms},

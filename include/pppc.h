@@ -125,6 +125,10 @@ typedef struct pppc_config {
     int32_t predictor;    /* 1: start each fine step's Newton from 2 u^m - u^{m-1} (default 1) */
     int32_t method;       /* pppc_method (default PPPC_METHOD_PPPC) */
     int32_t coarse_at;    /* pppc_coarse_at: where the coarse stiffness is frozen (default U^k) */
+    int32_t newton_schedule; /* 1: inexact PP-PC, the fine Newton tolerance of iteration k is
+                                max(tol_newton, min(1e-6, 1e-3 rel_res(U^{k-1}))): early
+                                iterates, whose jumps are large, are propagated less exactly;
+                                the last ones at tol_newton (default 0: always tol_newton) */
 } pppc_config;
 
 /* Iteration counts of the most recent iterate / solve / propagate call. */
@@ -346,8 +350,8 @@ pppc_status pppc_adjoint(pppc_handle* h, int32_t region, double tol, int32_t kma
  *
  * Errors of pppc_batch_create: INVALID_ARG (count < 1, NULL member,
  * duplicate), STATE (member without mesh, source), UNSUPPORTED (mixed
- * precisions or streams, PP-IC, a lane count that is not a power of two,
- * count > SMs), CUDA, NOMEM.  The message is in pppc_batch_last_error(NULL)
+ * precisions or streams, PP-IC, newton_schedule, a lane count that is not a
+ * power of two, count > SMs), CUDA, NOMEM.  The message is in pppc_batch_last_error(NULL)
  * after a failed create. */
 typedef struct pppc_batch pppc_batch;
 

@@ -26,6 +26,10 @@ thread_local std::string g_create_error;
 // with the Jacobian rounded to FP32 a solve cannot contract the FP64 Newton
 // residual by much more than ~1e-3, so tighter solves only burn iterations.
 constexpr double kFp32KrylovFloor = 1e-4;
+// Inexact PP-PC schedule: Newton tolerance min(kNewtonLoose, kNewtonFactor *
+// rel_res of the previous iterate), never below pppc_config.tol_newton.
+constexpr double kNewtonLoose = 1e-6;
+constexpr double kNewtonFactor = 1e-3;
 }
 
 
@@ -176,7 +180,11 @@ FineArgs pppc::detail::fine_args(pppc_handle* h, double* Fout) {
     a.n_fine = h->cfg.n_fine;
     a.dt = h->dt;
     a.inv_dt = 1.0 / h->dt;
-    a.tol_abs = h->cfg.tol_newton * h->gnorm * [&] {
+    // inexact PP-PC: looser Newton while the jumps are large (pppc_config.newton_schedule)
+    const double tol_newton = h->cfg.newton_schedule && std::isfinite(h->rr_prev)
+                                  ? std::max(h->cfg.tol_newton, std::min(kNewtonLoose, kNewtonFactor * h->rr_prev))
+                                  : (h->cfg.newton_schedule ? std::max(h->cfg.tol_newton, kNewtonLoose) : h->cfg.tol_newton);
+    a.tol_abs = tol_newton * h->gnorm * [&] {
         double s = 0.0;
         for (int j = 0; j < h->src.n_harm; ++j) s += std::fabs(h->src.amp[j]);
         return s;
@@ -527,6 +535,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (!(c.eta0 > 0.0) || !(c.eta0 < 1.0)) why = "eta0 must be in (0, 1)";
     else if (c.method != PPPC_METHOD_PPPC && c.method != PPPC_METHOD_PPIC) why = "unknown method";
     else if (c.coarse_at != PPPC_COARSE_AT_U && c.coarse_at != PPPC_COARSE_AT_F) why = "unknown coarse_at";
+    else if (c.newton_schedule != 0 && c.newton_schedule != 1) why = "newton_schedule must be 0 or 1";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
@@ -832,6 +841,7 @@ pppc_status pppc_set_state(pppc_handle* h, const double* U, int32_t on_device) {
     if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
     if (!U) return fail(h, PPPC_ERR_INVALID_ARG, "U is NULL");
     TRY(stage_in(h, U, on_device, h->U));
+    h->rr_prev = INFINITY;
     if (h->UN)  // PP-IC: the end-of-period state starts at U_0 (lane 0 of the lane layout)
         CK(cudaMemcpy2DAsync(h->UN, sizeof(double), h->U, (size_t)h->NB * sizeof(double), sizeof(double),
                              h->hm.ndof, cudaMemcpyDeviceToDevice, h->st));
@@ -878,6 +888,7 @@ pppc_status pppc_iterate(pppc_handle* h, double* rel_res) {
     TRY(begin_call(h));
     TRY(run_fine(h, h->U, h->F));
     TRY(run_jumps(h, h->U, h->F, rel_res));
+    h->rr_prev = h->stats.rel_res;
     TRY(run_update(h, h->U, h->F, h->Unext));
     CK(cudaStreamSynchronize(h->st));
     swap_state(h);
@@ -895,6 +906,7 @@ pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_
     for (int k = 0;; ++k) {
         TRY(run_fine(h, h->U, h->F));
         TRY(run_jumps(h, h->U, h->F, &rr));
+        h->rr_prev = rr;
         h->stats.fine_steps += h->cfg.n_fine;
         if (rr <= tol || k >= kmax) {
             if (iters) *iters = k;

@@ -483,6 +483,8 @@ pppc_status pppc_batch_create(pppc_handle* const* members, int32_t count, int32_
         if (h->fp32 != members[0]->fp32) return reject(PPPC_ERR_UNSUPPORTED, who + ": precisions differ");
         if (h->st != members[0]->st) return reject(PPPC_ERR_UNSUPPORTED, who + ": streams differ");
         if (h->cfg.method != PPPC_METHOD_PPPC) return reject(PPPC_ERR_UNSUPPORTED, who + ": PP-IC is not batched");
+        if (h->cfg.newton_schedule)
+            return reject(PPPC_ERR_UNSUPPORTED, who + ": the inexact Newton schedule is not batched");
         const int V = h->fp32 ? 4 : 2, G = h->NB / V;
         if (G < 1 || (G & (G - 1)) != 0 || G > 1024)
             return reject(PPPC_ERR_UNSUPPORTED, who + ": lanes / vector width must be a power of two");

@@ -59,6 +59,7 @@ struct pppc_handle {
     SourceDev src{};
     double gnorm = 0.0, src_area = 0.0;
     pppc_stats stats{};
+    double rr_prev = INFINITY;   // rel_res of the previous iteration (inexact PP-PC schedule)
     // per nonlinear element: its region; per region: sigma (for the adjoint)
     std::vector<int> nl_region;
     std::vector<double> region_sigma;

@@ -303,3 +303,21 @@ def test_pppc_at_fine_results_matches_oracle():
     assert ref.converged and rr <= 1e-11
     assert abs(iters - ref.iterations) <= 1
     assert rel(free(prob, U), ref.U) < TOL64
+
+
+def test_inexact_newton_schedule_keeps_the_fixed_point():
+    """newton_schedule = 1 propagates early iterates with a looser Newton
+    tolerance; the periodic solution it converges to is the oracle's."""
+    prob = workload("small")
+    m = FEModel(prob)
+    with gpu_solver(prob, tol_coarse=1e-12, newton_schedule=True) as s:
+        iters, rr = s.solve_periodic(tol=1e-11, kmax=40)
+        U = s.get_state()
+        st = s.stats()
+    with gpu_solver(prob, tol_coarse=1e-12) as s:
+        s.solve_periodic(tol=1e-11, kmax=40)
+        st0 = s.stats()
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=40)
+    assert rr <= 1e-11
+    assert rel(free(prob, U), ref.U) < TOL64
+    assert st["newton_iters"] < st0["newton_iters"]
