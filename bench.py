@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--tts-schedule", type=int, default=1, choices=[0, 1],
                     help="time-to-steady-state run: 1 = inexact PP-PC (same fixed point, final iterates at the "
                          "full Newton tolerance)")
+    ap.add_argument("--precond", default="tridiag", choices=["jacobi", "tridiag"],
+                    help="fine PCG preconditioner")
     ap.add_argument("--coarse-at", default="U", choices=["U", "F"],
                     help="freeze the coarse stiffness at U^k or at the fine results F^k")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady-state run")
@@ -328,16 +330,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB: int) -> float:
+def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB: int, tri: bool = False) -> float:
     """Algorithmic bytes of one PCG iteration per (row, lane) of the fine
     propagator (single-reduction CG, two phases): phase A reads z, r and
     writes w; phase B reads z, w, p, s, r, u and writes p, s, r, z, u.  Vectors
     are FP32 in the mixed path (u stays FP64).  Matrix: per-lane values on the
-    special rows, shared values and column indices amortised over the lanes."""
+    special rows, shared values and column indices amortised over the lanes.
+    With the tridiagonal-chunk preconditioner phase B also reads the
+    multiplier and inverse pivot of every row and writes and re-reads the
+    forward-substituted vector, in place of the Jacobi diagonal."""
     v = 4.0 if mixed else 8.0
     phase_a = 3 * v
     phase_b = 5 * v + 8.0 + 4 * v + 8.0
     diag = special_frac * v + (1 - special_frac) * v / NB
+    if tri:
+        diag = 2 * v + 2 * v
     matrix = special_frac * nnz_row * v + (1 - special_frac) * nnz_row * (v + 4.0) / NB \
         + special_frac * nnz_row * 4.0 / NB
     return phase_a + phase_b + diag + matrix
@@ -455,7 +462,7 @@ def main():
     prob = workload(WORKLOAD)
     mixed = args.precision == "mixed"
     solver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
-                          newton_schedule=bool(args.newton_schedule), stream=stream)
+                          newton_schedule=bool(args.newton_schedule), precond=args.precond, stream=stream)
     ndof = solver.ndof
     units_per_step = prob.N * prob.n_fine * ndof
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -497,7 +504,7 @@ def main():
     mc = solver.mesh_counts()
     nnz_row = mc["nnz"] / mc["ndof"]
     sp_frac = mc["special_rows"] / mc["ndof"]
-    bpr = pcg_bytes_per_row_lane(mixed, sp_frac, nnz_row, prob.N)
+    bpr = pcg_bytes_per_row_lane(mixed, sp_frac, nnz_row, prob.N, tri=args.precond == "tridiag")
     fine_s = sum(fine_ms) * 1e-3
     pcg_bytes = bpr * ndof * prob.N * pcg
     hbm_peak, peak_src = peaks()
@@ -532,7 +539,7 @@ def main():
     tts = None
     if not args.no_tts:
         tsolver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
-                               newton_schedule=bool(args.tts_schedule), stream=stream)
+                               newton_schedule=bool(args.tts_schedule), precond=args.precond, stream=stream)
         tsolver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -562,7 +569,8 @@ def main():
         "config": {"workload": "coax medium: nr=100 x ntheta=200 (19801 DOFs), N=64, 50 fine steps, "
                                "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
                    "parallelism": "replicas only", "l2": "flushed between steps (512 MB write)",
-                   "coarse_at": args.coarse_at, "newton_schedule": args.newton_schedule},
+                   "coarse_at": args.coarse_at, "newton_schedule": args.newton_schedule,
+                   "precond": args.precond},
         "time_to_steady_state": tts,
         "per_step": {"pcg_iters": pcg / args.steps, "newton_iters": newton / args.steps,
                      "fine_ms": sum(fine_ms) / args.steps, "step_ms": step_ms},

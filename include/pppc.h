@@ -129,6 +129,9 @@ typedef struct pppc_config {
                                 max(tol_newton, min(1e-6, 1e-3 rel_res(U^{k-1}))): early
                                 iterates, whose jumps are large, are propagated less exactly;
                                 the last ones at tol_newton (default 0: always tol_newton) */
+    int32_t precond;      /* fine PCG preconditioner: 0 Jacobi (default); 1 the tridiagonal part of
+                             every 4 consecutive rows, factorised per lane (row order should follow
+                             the mesh's strongest couplings, e.g. the rings of a polar mesh) */
 } pppc_config;
 
 /* Iteration counts of the most recent iterate / solve / propagate call. */

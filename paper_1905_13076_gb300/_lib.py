@@ -38,7 +38,7 @@ class pppc_config(ctypes.Structure):
         ("tol_lin", c_double), ("max_lin", c_int32), ("tol_coarse", c_double),
         ("max_coarse", c_int32), ("stream", c_void_p), ("alloc", c_void_p),
         ("free_fn", c_void_p), ("alloc_ctx", c_void_p), ("eta0", c_double), ("predictor", c_int32),
-        ("method", c_int32), ("coarse_at", c_int32), ("newton_schedule", c_int32),
+        ("method", c_int32), ("coarse_at", c_int32), ("newton_schedule", c_int32), ("precond", c_int32),
     ]
 
 

@@ -29,6 +29,8 @@ constexpr double kFp32KrylovFloor = 1e-4;
 // Inexact PP-PC schedule: Newton tolerance min(kNewtonLoose, kNewtonFactor *
 // rel_res of the previous iterate), never below pppc_config.tol_newton.
 constexpr double kNewtonLoose = 1e-6;
+// Rows per tridiagonal chunk of the fine PCG preconditioner (pppc_config.precond = 1).
+constexpr int kTriChunk = 4;
 constexpr double kNewtonFactor = 1e-3;
 }
 
@@ -194,6 +196,12 @@ FineArgs pppc::detail::fine_args(pppc_handle* h, double* Fout) {
     a.predictor = h->cfg.predictor;
     a.x = h->x;
     a.dx = h->dx;
+    if (h->cfg.precond == 1) {
+        a.tri = kTriChunk;
+        a.tri_low = h->d_tri_low;
+        a.tri_m = h->tri_m;
+        a.tri_ie = h->tri_ie;
+    }
     a.max_newton = h->cfg.max_newton;
     a.max_lin = h->cfg.max_lin;
     a.u = Fout;
@@ -536,6 +544,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (c.method != PPPC_METHOD_PPPC && c.method != PPPC_METHOD_PPIC) why = "unknown method";
     else if (c.coarse_at != PPPC_COARSE_AT_U && c.coarse_at != PPPC_COARSE_AT_F) why = "unknown coarse_at";
     else if (c.newton_schedule != 0 && c.newton_schedule != 1) why = "newton_schedule must be 0 or 1";
+    else if (c.precond != 0 && c.precond != 1) why = "precond must be 0 or 1";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
@@ -755,6 +764,16 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         *v = dev_alloc(h, LV * ts);
         if (!*v) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
         CK(cudaMemsetAsync(*v, 0, LV * ts, h->st));
+    }
+    if (h->cfg.precond == 1) {
+        std::vector<int> low(hm.ndof, -1);
+        for (int i = 1; i < hm.ndof; ++i)
+            for (int k = hm.rowptr[i]; k < hm.rowptr[i + 1]; ++k)
+                if (hm.col[k] == i - 1) low[i] = k;
+        TRY(upload(h, &h->d_tri_low, low));
+        h->tri_m = dev_alloc(h, LV * ts);
+        h->tri_ie = dev_alloc(h, LV * ts);
+        if (!h->tri_m || !h->tri_ie) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
     }
     h->J = dev_alloc(h, (size_t)hm.n_slots * h->NB * ts);
     h->invd = dev_alloc(h, (size_t)hm.n_sp * h->NB * ts);

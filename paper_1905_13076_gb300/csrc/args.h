@@ -106,6 +106,11 @@ struct FineArgs {
     double* lam_out;         // adjoint: [n_fine][ndof][NB] lambda at levels 1..n_fine, or null
     double tol_rel;          // adjoint: a level is solved when ||R|| <= tol_rel ||b||
     double g_scale;          // adjoint: 2 / (T dt), the loss weight of the adjoint source
+    // preconditioner: 0 = Jacobi; c > 0 = tridiagonal blocks of c consecutive rows
+    int tri;
+    const int* tri_low;      // [ndof] CSR index of entry (i, i-1), -1 if absent
+    void* tri_m;             // [ndof*NB] of T: LDL^T multipliers of the chunk factorisation
+    void* tri_ie;            // [ndof*NB] of T: inverse pivots
 };
 
 // One record per Newton test of the fine sweep:

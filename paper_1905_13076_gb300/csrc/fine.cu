@@ -433,6 +433,154 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
     }
 }
 
+// Matrix entry (i, k) of the Newton matrix for this thread's lanes, given
+// its CSR index kk: per lane on special rows (J), shared K_lin elsewhere.
+template <typename T, int V>
+__device__ __forceinline__ Lanes<T, V> entry(const MeshDev& m, const T* KlinT, const T* J, int i, int kk, int NB,
+                                           int l0) {
+    const int slot0 = m.row_slot[i];
+    if (slot0 >= 0) return ldv<T, V>(J + (size_t)(slot0 + kk - m.rowptr[i]) * NB + l0);
+    Lanes<T, V> v;
+    const T k = KlinT[kk];
+#pragma unroll
+    for (int h = 0; h < V; ++h) v.v[h] = k;
+    return v;
+}
+
+// Tridiagonal-chunk preconditioner.  The own rows [rs, re) are cut into
+// chunks of a.tri consecutive rows, chunk q handled by row group q mod RB.
+// Each chunk's tridiagonal part T_c of the Newton matrix (diagonal and the
+// (i, i-1) / (i-1, i) couplings; row order follows the mesh's strongest
+// couplings, along the rings of a polar mesh) is factorised per lane as
+// L D L^T (multipliers tri_m, inverse pivots tri_ie, FP64 arithmetic), and
+// z = T_c^-1 r replaces the Jacobi z = D^-1 r.  tri_factor factorises and
+// applies it to the r of the residual phase (z, and (r, z) into accz);
+// tri_update is the PCG vector update with z from the chunk solves.
+template <typename T, int V>
+__device__ __noinline__ void tri_factor(const FineArgs& a, const MeshDev& m, int rs, int re, int RB, int rb, int l0,
+                                        T* accz) {
+    const int NB = a.NB, c = a.tri;
+    const T* KlinT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.Klin32)
+                                                   : reinterpret_cast<const T*>(m.Klin);
+    const T* J = static_cast<const T*>(a.J);
+    const T* r = static_cast<const T*>(a.r);
+    T* z = static_cast<T*>(a.z);
+    T* tm = static_cast<T*>(a.tri_m);
+    T* tie = static_cast<T*>(a.tri_ie);
+    for (int k0 = rs + rb * c; k0 < re; k0 += RB * c) {
+        const int k1 = min(k0 + c, re) - 1;
+        double e[V], y[V];
+        for (int k = k0; k <= k1; ++k) {
+            const size_t o = (size_t)k * NB + l0;
+            const Lanes<T, V> d = entry<T, V>(m, KlinT, J, k, m.diag_k[k], NB, l0);
+            const Lanes<T, V> rk = ldv<T, V>(r + o);
+            const int lk = a.tri_low[k];
+            Lanes<T, V> mk, ie, yk;
+            if (k > k0 && lk >= 0) {
+                const Lanes<T, V> l = entry<T, V>(m, KlinT, J, k, lk, NB, l0);
+#pragma unroll
+                for (int h = 0; h < V; ++h) {
+                    const double mu = (double)l.v[h] / e[h];
+                    e[h] = (double)d.v[h] - mu * (double)l.v[h];
+                    y[h] = (double)rk.v[h] - mu * y[h];
+                    mk.v[h] = (T)mu;
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < V; ++h) {
+                    e[h] = (double)d.v[h];
+                    y[h] = (double)rk.v[h];
+                    mk.v[h] = (T)0;
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < V; ++h) {
+                ie.v[h] = (T)(1.0 / e[h]);
+                yk.v[h] = (T)y[h];
+            }
+            stv<T, V>(tm + o, mk);
+            stv<T, V>(tie + o, ie);
+            stv<T, V>(z + o, yk);   // forward-substituted y, replaced below
+        }
+        Lanes<T, V> zn;
+        for (int k = k1; k >= k0; --k) {
+            const size_t o = (size_t)k * NB + l0;
+            const Lanes<T, V> yk = ldv<T, V>(z + o);
+            const Lanes<T, V> ie = ldv<T, V>(tie + o);
+            const Lanes<T, V> rk = ldv<T, V>(r + o);
+            Lanes<T, V> mn;
+            if (k < k1) mn = ldv<T, V>(tm + o + NB);
+            Lanes<T, V> zk;
+#pragma unroll
+            for (int h = 0; h < V; ++h) {
+                zk.v[h] = yk.v[h] * ie.v[h] - (k < k1 ? mn.v[h] * zn.v[h] : (T)0);
+                accz[h] += rk.v[h] * zk.v[h];
+            }
+            stv<T, V>(z + o, zk);
+            zn = zk;
+        }
+    }
+}
+
+template <typename T, int V>
+__device__ __noinline__ void tri_update(const FineArgs& a, int rs, int re, int RB, int rb, int l0, const double* s_alpha,
+                                        const double* s_beta, T* pB, T* sB, T* xB, const T* wB, size_t vo, size_t wo) {
+    const int NB = a.NB, c = a.tri;
+    T* r = static_cast<T*>(a.r);
+    T* z = static_cast<T*>(a.z);
+    const T* tm = static_cast<const T*>(a.tri_m);
+    const T* tie = static_cast<const T*>(a.tri_ie);
+    T alv[V], bev[V];
+#pragma unroll
+    for (int h = 0; h < V; ++h) {
+        alv[h] = (T)s_alpha[l0 + h];
+        bev[h] = (T)s_beta[l0 + h];
+    }
+    for (int k0 = rs + rb * c; k0 < re; k0 += RB * c) {
+        const int k1 = min(k0 + c, re) - 1;
+        Lanes<T, V> yp;
+        for (int k = k0; k <= k1; ++k) {
+            const size_t o = (size_t)k * NB + l0;
+            const size_t ov = o - vo;
+            const Lanes<T, V> zi = ldv<T, V>(z + o);
+            const Lanes<T, V> wi = ldv<T, V>(wB + (o - wo));
+            const Lanes<T, V> pi = ldv<T, V>(pB + ov);
+            const Lanes<T, V> si = ldv<T, V>(sB + ov);
+            const Lanes<T, V> ri = ldv<T, V>(r + o);
+            const Lanes<T, V> xi = ldv<T, V>(xB + ov);
+            const Lanes<T, V> mk = ldv<T, V>(tm + o);
+            Lanes<T, V> pn, sn, rn, xn, yk;
+#pragma unroll
+            for (int h = 0; h < V; ++h) {
+                pn.v[h] = zi.v[h] + bev[h] * pi.v[h];
+                sn.v[h] = wi.v[h] + bev[h] * si.v[h];
+                rn.v[h] = ri.v[h] - alv[h] * sn.v[h];
+                xn.v[h] = xi.v[h] + alv[h] * pn.v[h];
+                yk.v[h] = rn.v[h] - (k > k0 ? mk.v[h] * yp.v[h] : (T)0);
+            }
+            stv<T, V>(pB + ov, pn);
+            stv<T, V>(sB + ov, sn);
+            stv<T, V>(r + o, rn);
+            stv<T, V>(xB + ov, xn);
+            stv<T, V>(z + o, yk);   // forward-substituted y, replaced below
+            yp = yk;
+        }
+        Lanes<T, V> zn;
+        for (int k = k1; k >= k0; --k) {
+            const size_t o = (size_t)k * NB + l0;
+            const Lanes<T, V> yk = ldv<T, V>(z + o);
+            const Lanes<T, V> ie = ldv<T, V>(tie + o);
+            Lanes<T, V> mn;
+            if (k < k1) mn = ldv<T, V>(tm + o + NB);
+            Lanes<T, V> zk;
+#pragma unroll
+            for (int h = 0; h < V; ++h) zk.v[h] = yk.v[h] * ie.v[h] - (k < k1 ? mn.v[h] * zn.v[h] : (T)0);
+            stv<T, V>(z + o, zk);
+            zn = zk;
+        }
+    }
+}
+
 // On this thread's rows and lanes: u += x and dx = x for lanes that took a
 // Newton step (coef 1), u += coef * dx for lanes that backtrack (coef < 0),
 // nothing for the others.  Out of line for the same reason as residual_rows.
@@ -605,6 +753,13 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                 adjoint_rows<T, V>(a, m, row0, re, RB, l0, j, accR, accz, accb, xB, vo);
             else
                 residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo);
+            if (a.tri > 0) {
+                // the chunk preconditioner replaces z = D^-1 r (r of other threads' rows: sync)
+                __syncthreads();
+#pragma unroll
+                for (int h = 0; h < V; ++h) accz[h] = 0;
+                tri_factor<T, V>(a, m, rs, re, RB, rb, l0, accz);
+            }
             {
                 RT v[NV][V];
 #pragma unroll
@@ -850,6 +1005,11 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     ++s_cnt[2];
                 }
 
+                if (a.tri > 0) {
+                    tri_update<T, V>(a, rs, re, RB, rb, l0, s_alpha, s_beta, pB, sB, xB, wB, vo, wo);
+                    if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+                    continue;
+                }
                 T alv[V], bev[V];
 #pragma unroll
                 for (int h = 0; h < V; ++h) {

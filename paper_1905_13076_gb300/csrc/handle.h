@@ -60,6 +60,8 @@ struct pppc_handle {
     double gnorm = 0.0, src_area = 0.0;
     pppc_stats stats{};
     double rr_prev = INFINITY;   // rel_res of the previous iteration (inexact PP-PC schedule)
+    int* d_tri_low = nullptr;    // tridiagonal-chunk preconditioner: CSR index of (i, i-1)
+    void *tri_m = nullptr, *tri_ie = nullptr;
     // per nonlinear element: its region; per region: sigma (for the adjoint)
     std::vector<int> nl_region;
     std::vector<double> region_sigma;

@@ -43,7 +43,7 @@ class PPPC:
                  coarse_lin: str = "avg_jacobian", tol_newton: float = 1e-10, max_newton: int = 30,
                  tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
                  max_coarse: int = 20000, eta0: float = 1e-2, predictor: bool = True, method: str = "pppc",
-                 coarse_at: str = "U", newton_schedule: bool = False, stream=None):
+                 coarse_at: str = "U", newton_schedule: bool = False, precond: str = "jacobi", stream=None):
         self._lib = _lib.load()
         cfg = pppc_config()
         self._lib.pppc_config_default(ctypes.byref(cfg))
@@ -57,6 +57,7 @@ class PPPC:
         cfg.method = _lib.METHODS[method]
         cfg.coarse_at = _lib.COARSE_AT[coarse_at]
         cfg.newton_schedule = int(bool(newton_schedule))
+        cfg.precond = {"jacobi": 0, "tridiag": 1}[precond]
         cfg.stream = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
         self.cfg = cfg
         h = ctypes.c_void_p()

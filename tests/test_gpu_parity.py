@@ -321,3 +321,27 @@ def test_inexact_newton_schedule_keeps_the_fixed_point():
     assert rr <= 1e-11
     assert rel(free(prob, U), ref.U) < TOL64
     assert st["newton_iters"] < st0["newton_iters"]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("mixed", TOL_MIXED)])
+def test_tridiagonal_chunk_preconditioner_matches_oracle(precision, tol):
+    """precond = tridiag changes only the fine PCG's preconditioner: the fine
+    sweep and the periodic solution are the oracle's, with fewer PCG
+    iterations."""
+    prob = workload("small")
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    ref = fine_sweep(m, free(prob, U0), prob.N, prob.n_fine, prob.T)
+    with gpu_solver(prob, precision=precision, precond="tridiag", tol_lin=1e-12 if precision == "fp64" else 1e-6) as s:
+        F = s.propagate_fine(U0)
+        pcg_tri = s.stats()["pcg_iters"]
+    with gpu_solver(prob, precision=precision, tol_lin=1e-12 if precision == "fp64" else 1e-6) as s:
+        s.propagate_fine(U0)
+        pcg_jac = s.stats()["pcg_iters"]
+    assert rel(free(prob, F), ref) < tol
+    assert pcg_tri < pcg_jac
+    with gpu_solver(prob, precision=precision, precond="tridiag", tol_coarse=1e-12) as s:
+        iters, rr = s.solve_periodic(tol=1e-11 if precision == "fp64" else 1e-9, kmax=40)
+        U = s.get_state()
+    pp = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=40)
+    assert rel(free(prob, U), pp.U) < tol
