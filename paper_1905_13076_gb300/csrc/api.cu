@@ -29,7 +29,8 @@ constexpr double kFp32KrylovFloor = 1e-4;
 // Inexact PP-PC schedule: Newton tolerance min(kNewtonLoose, kNewtonFactor *
 // rel_res of the previous iterate), never below pppc_config.tol_newton.
 constexpr double kNewtonLoose = 1e-6;
-// Rows per tridiagonal chunk of the fine PCG preconditioner (pppc_config.precond = 1).
+// Rows per tridiagonal chunk of the fine PCG preconditioner (pppc_config.precond
+// = 1); the kernel's chunk solve is specialised for it (kTri in fine.cu).
 constexpr int kTriChunk = 4;
 constexpr double kNewtonFactor = 1e-3;
 }

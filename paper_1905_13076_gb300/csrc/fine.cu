@@ -522,62 +522,48 @@ __device__ __noinline__ void tri_factor(const FineArgs& a, const MeshDev& m, int
     }
 }
 
+// z = T_c^-1 r on this row group's chunks with the stored factorisation
+// (after the PCG update of r by all threads and a __syncthreads).  Chunks
+// have kTri rows: all of a chunk's loads are issued first, then the forward
+// and back substitution run in registers (rows past the block's end act as
+// zero rows).
+constexpr int kTri = 4;
 template <typename T, int V>
-__device__ __noinline__ void tri_update(const FineArgs& a, int rs, int re, int RB, int rb, int l0, const double* s_alpha,
-                                        const double* s_beta, T* pB, T* sB, T* xB, const T* wB, size_t vo, size_t wo) {
-    const int NB = a.NB, c = a.tri;
-    T* r = static_cast<T*>(a.r);
+__device__ __noinline__ void tri_solve(const FineArgs& a, int rs, int re, int RB, int rb, int l0) {
+    const int NB = a.NB;
+    const T* r = static_cast<const T*>(a.r);
     T* z = static_cast<T*>(a.z);
     const T* tm = static_cast<const T*>(a.tri_m);
     const T* tie = static_cast<const T*>(a.tri_ie);
-    T alv[V], bev[V];
+    for (int k0 = rs + rb * kTri; k0 < re; k0 += RB * kTri) {
+        Lanes<T, V> rv[kTri], mv[kTri], iv[kTri];
 #pragma unroll
-    for (int h = 0; h < V; ++h) {
-        alv[h] = (T)s_alpha[l0 + h];
-        bev[h] = (T)s_beta[l0 + h];
-    }
-    for (int k0 = rs + rb * c; k0 < re; k0 += RB * c) {
-        const int k1 = min(k0 + c, re) - 1;
-        Lanes<T, V> yp;
-        for (int k = k0; k <= k1; ++k) {
-            const size_t o = (size_t)k * NB + l0;
-            const size_t ov = o - vo;
-            const Lanes<T, V> zi = ldv<T, V>(z + o);
-            const Lanes<T, V> wi = ldv<T, V>(wB + (o - wo));
-            const Lanes<T, V> pi = ldv<T, V>(pB + ov);
-            const Lanes<T, V> si = ldv<T, V>(sB + ov);
-            const Lanes<T, V> ri = ldv<T, V>(r + o);
-            const Lanes<T, V> xi = ldv<T, V>(xB + ov);
-            const Lanes<T, V> mk = ldv<T, V>(tm + o);
-            Lanes<T, V> pn, sn, rn, xn, yk;
+        for (int q = 0; q < kTri; ++q) {
+            if (k0 + q < re) {
+                const size_t o = (size_t)(k0 + q) * NB + l0;
+                rv[q] = ldv<T, V>(r + o);
+                mv[q] = ldv<T, V>(tm + o);
+                iv[q] = ldv<T, V>(tie + o);
+            } else {
 #pragma unroll
-            for (int h = 0; h < V; ++h) {
-                pn.v[h] = zi.v[h] + bev[h] * pi.v[h];
-                sn.v[h] = wi.v[h] + bev[h] * si.v[h];
-                rn.v[h] = ri.v[h] - alv[h] * sn.v[h];
-                xn.v[h] = xi.v[h] + alv[h] * pn.v[h];
-                yk.v[h] = rn.v[h] - (k > k0 ? mk.v[h] * yp.v[h] : (T)0);
+                for (int h = 0; h < V; ++h) rv[q].v[h] = mv[q].v[h] = iv[q].v[h] = (T)0;
             }
-            stv<T, V>(pB + ov, pn);
-            stv<T, V>(sB + ov, sn);
-            stv<T, V>(r + o, rn);
-            stv<T, V>(xB + ov, xn);
-            stv<T, V>(z + o, yk);   // forward-substituted y, replaced below
-            yp = yk;
         }
-        Lanes<T, V> zn;
-        for (int k = k1; k >= k0; --k) {
-            const size_t o = (size_t)k * NB + l0;
-            const Lanes<T, V> yk = ldv<T, V>(z + o);
-            const Lanes<T, V> ie = ldv<T, V>(tie + o);
-            Lanes<T, V> mn;
-            if (k < k1) mn = ldv<T, V>(tm + o + NB);
-            Lanes<T, V> zk;
+        // forward: y_q = r_q - m_q y_{q-1} (m_0 is 0), in place in rv
 #pragma unroll
-            for (int h = 0; h < V; ++h) zk.v[h] = yk.v[h] * ie.v[h] - (k < k1 ? mn.v[h] * zn.v[h] : (T)0);
-            stv<T, V>(z + o, zk);
-            zn = zk;
-        }
+        for (int q = 1; q < kTri; ++q)
+#pragma unroll
+            for (int h = 0; h < V; ++h) rv[q].v[h] -= mv[q].v[h] * rv[q - 1].v[h];
+        // back: z_q = y_q / e_q - m_{q+1} z_{q+1}, in place in rv
+#pragma unroll
+        for (int h = 0; h < V; ++h) rv[kTri - 1].v[h] *= iv[kTri - 1].v[h];
+#pragma unroll
+        for (int q = kTri - 2; q >= 0; --q)
+#pragma unroll
+            for (int h = 0; h < V; ++h) rv[q].v[h] = rv[q].v[h] * iv[q].v[h] - mv[q + 1].v[h] * rv[q + 1].v[h];
+#pragma unroll
+        for (int q = 0; q < kTri; ++q)
+            if (k0 + q < re) stv<T, V>(z + (size_t)(k0 + q) * NB + l0, rv[q]);
     }
 }
 
@@ -1005,11 +991,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     ++s_cnt[2];
                 }
 
-                if (a.tri > 0) {
-                    tri_update<T, V>(a, rs, re, RB, rb, l0, s_alpha, s_beta, pB, sB, xB, wB, vo, wo);
-                    if (!grid_sync(a.bar, a.status, bid, nblk)) return;
-                    continue;
-                }
+                const bool tri = a.tri > 0;
                 T alv[V], bev[V];
 #pragma unroll
                 for (int h = 0; h < V; ++h) {
@@ -1026,29 +1008,37 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     const Lanes<T, V> si = ldv<T, V>(sB + ov);
                     const Lanes<T, V> ri = ldv<T, V>(r + o);
                     const Lanes<T, V> xi = ldv<T, V>(xB + ov);
-                    Lanes<T, V> ivl;
-                    const int sp = m.sp_index[i];
-                    if (sp < 0) {
-                        const T d = invdiag_linT[i];
-#pragma unroll
-                        for (int h = 0; h < V; ++h) ivl.v[h] = d;
-                    } else {
-                        ivl = ldv<T, V>(invd + (size_t)sp * NB + l0);
-                    }
-                    Lanes<T, V> pn, sn, rn, zn, xn;
+                    Lanes<T, V> pn, sn, rn, xn;
 #pragma unroll
                     for (int h = 0; h < V; ++h) {
                         pn.v[h] = zi.v[h] + bev[h] * pi.v[h];
                         sn.v[h] = wi.v[h] + bev[h] * si.v[h];
                         rn.v[h] = ri.v[h] - alv[h] * sn.v[h];
-                        zn.v[h] = rn.v[h] * ivl.v[h];
                         xn.v[h] = xi.v[h] + alv[h] * pn.v[h];
                     }
                     stv<T, V>(pB + ov, pn);
                     stv<T, V>(sB + ov, sn);
                     stv<T, V>(r + o, rn);
-                    stv<T, V>(z + o, zn);
                     stv<T, V>(xB + ov, xn);
+                    if (!tri) {
+                        // Jacobi: z = D^-1 r
+                        Lanes<T, V> ivl, zn;
+                        const int sp = m.sp_index[i];
+                        if (sp < 0) {
+                            const T d = invdiag_linT[i];
+#pragma unroll
+                            for (int h = 0; h < V; ++h) ivl.v[h] = d;
+                        } else {
+                            ivl = ldv<T, V>(invd + (size_t)sp * NB + l0);
+                        }
+#pragma unroll
+                        for (int h = 0; h < V; ++h) zn.v[h] = rn.v[h] * ivl.v[h];
+                        stv<T, V>(z + o, zn);
+                    }
+                }
+                if (tri) {
+                    __syncthreads();   // the chunks' r were updated by other row groups
+                    tri_solve<T, V>(a, rs, re, RB, rb, l0);
                 }
                 if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             }
