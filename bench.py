@@ -125,7 +125,8 @@ def run_adjoint(args, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     prob = workload("adjoint")
-    s = from_problem(prob, precision=args.precision, stream=stream)
+    s = from_problem(prob, precision=args.precision, precond=args.precond,
+                     newton_schedule=bool(args.tts_schedule), stream=stream)
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         its, rr = s.solve_periodic(tol=1e-10, kmax=80, raise_on_fail=False)
@@ -144,7 +145,8 @@ def run_adjoint(args, local):
         "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": "coax adjoint case: nr=160 x ntheta=320 (50881 DOFs), N=128, 40 fine steps, "
-                               "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision},
+                               "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
+                   "precond": args.precond, "newton_schedule": args.tts_schedule},
         "forward": {"seconds": fwd_s, "host_seconds": t_fwd_host, "pppc_iterations": its, "rel_res": rr,
                     "fine_dof_steps_per_s": units * (its + 1) / (fst["fine_ms"] * 1e-3)},
         "adjoint": {"seconds": adj_s, "host_seconds": t_adj_host, "pppc_iterations": info["iterations"],
@@ -179,7 +181,8 @@ def run_batched(args, local):
     probs = batched_cables()
     # Kbar frozen at the fine results: a cold start of a 50 A cable linearised at
     # U = 0 (small-field reluctivity) sends the first coarse update far past saturation
-    members = [from_problem(p, precision=args.precision, coarse_at="F", max_newton=100, stream=stream)
+    members = [from_problem(p, precision=args.precision, coarse_at="F", max_newton=100, precond=args.precond,
+                            stream=stream)
                for p in probs]
     units = sum(p.N * p.n_fine * m.ndof for p, m in zip(probs, members))
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -190,7 +193,8 @@ def run_batched(args, local):
         tot = 0.0
         for p, m in zip(probs, ms):
             mc = m.mesh_counts()
-            bpr = pcg_bytes_per_row_lane(mixed, mc["special_rows"] / mc["ndof"], mc["nnz"] / mc["ndof"], p.N)
+            bpr = pcg_bytes_per_row_lane(mixed, mc["special_rows"] / mc["ndof"], mc["nnz"] / mc["ndof"], p.N,
+                                         tri=args.precond == "tridiag")
             tot += bpr * mc["ndof"] * p.N * m.stats()["pcg_iters"]
         return tot
 
@@ -246,6 +250,7 @@ def run_batched(args, local):
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": "32 coax cables, seed 2026: nr 20-200, ntheta 40-400, 1-50 A, sigma 1e6-3e7, "
                                "N in {16,32,64}, 20-50 fine steps", "precision": args.precision,
+                   "precond": args.precond,
                    "fine_dof_steps_per_step": units, "l2": "flushed between steps (512 MB write)"},
         "sequential_single_handles": {"value": seq_value, "unit": UNIT, "ms": seq_ms},
         "batched_over_sequential": value / seq_value,
