@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--tts-schedule", type=int, default=1, choices=[0, 1],
                     help="time-to-steady-state run: 1 = inexact PP-PC (same fixed point, final iterates at the "
                          "full Newton tolerance)")
+    ap.add_argument("--tol-coarse", type=float, default=1e-3,
+                    help="relative tolerance of the harmonic (COCG) solves of the medium run (their right-hand "
+                         "side is the jumps, so a relative tolerance shrinks the absolute error with them)")
     ap.add_argument("--precond", default="tridiag", choices=["jacobi", "tridiag"],
                     help="fine PCG preconditioner")
     ap.add_argument("--coarse-at", default="U", choices=["U", "F"],
@@ -467,7 +470,8 @@ def main():
     prob = workload(WORKLOAD)
     mixed = args.precision == "mixed"
     solver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
-                          newton_schedule=bool(args.newton_schedule), precond=args.precond, stream=stream)
+                          newton_schedule=bool(args.newton_schedule), precond=args.precond,
+                          tol_coarse=args.tol_coarse, stream=stream)
     ndof = solver.ndof
     units_per_step = prob.N * prob.n_fine * ndof
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -544,7 +548,8 @@ def main():
     tts = None
     if not args.no_tts:
         tsolver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
-                               newton_schedule=bool(args.tts_schedule), precond=args.precond, stream=stream)
+                               newton_schedule=bool(args.tts_schedule), precond=args.precond,
+                               tol_coarse=args.tol_coarse, stream=stream)
         tsolver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -575,7 +580,7 @@ def main():
                                "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
                    "parallelism": "replicas only", "l2": "flushed between steps (512 MB write)",
                    "coarse_at": args.coarse_at, "newton_schedule": args.newton_schedule,
-                   "precond": args.precond},
+                   "precond": args.precond, "tol_coarse": args.tol_coarse},
         "time_to_steady_state": tts,
         "per_step": {"pcg_iters": pcg / args.steps, "newton_iters": newton / args.steps,
                      "fine_ms": sum(fine_ms) / args.steps, "step_ms": step_ms},
