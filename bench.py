@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--tol-coarse", type=float, default=1e-3,
                     help="relative tolerance of the harmonic (COCG) solves of the medium run (their right-hand "
                          "side is the jumps, so a relative tolerance shrinks the absolute error with them)")
+    ap.add_argument("--predictor", type=int, default=2, choices=[0, 1, 2],
+                    help="Newton start: 0 previous level, 1 linear, 2 quadratic extrapolation")
     ap.add_argument("--precond", default="tridiag", choices=["jacobi", "tridiag"],
                     help="fine PCG preconditioner")
     ap.add_argument("--coarse-at", default="U", choices=["U", "F"],
@@ -128,8 +130,8 @@ def run_adjoint(args, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     prob = workload("adjoint")
-    s = from_problem(prob, precision=args.precision, precond=args.precond,
-                     newton_schedule=bool(args.tts_schedule), stream=stream)
+    s = from_problem(prob, precision=args.precision, precond=args.precond, predictor=args.predictor,
+                     tol_coarse=args.tol_coarse, newton_schedule=bool(args.tts_schedule), stream=stream)
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         its, rr = s.solve_periodic(tol=1e-10, kmax=80, raise_on_fail=False)
@@ -149,7 +151,8 @@ def run_adjoint(args, local):
         "data": "synthetic",
         "config": {"workload": "coax adjoint case: nr=160 x ntheta=320 (50881 DOFs), N=128, 40 fine steps, "
                                "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
-                   "precond": args.precond, "newton_schedule": args.tts_schedule},
+                   "precond": args.precond, "newton_schedule": args.tts_schedule, "predictor": args.predictor,
+                   "tol_coarse": args.tol_coarse},
         "forward": {"seconds": fwd_s, "host_seconds": t_fwd_host, "pppc_iterations": its, "rel_res": rr,
                     "fine_dof_steps_per_s": units * (its + 1) / (fst["fine_ms"] * 1e-3)},
         "adjoint": {"seconds": adj_s, "host_seconds": t_adj_host, "pppc_iterations": info["iterations"],
@@ -185,7 +188,7 @@ def run_batched(args, local):
     # Kbar frozen at the fine results: a cold start of a 50 A cable linearised at
     # U = 0 (small-field reluctivity) sends the first coarse update far past saturation
     members = [from_problem(p, precision=args.precision, coarse_at="F", max_newton=100, precond=args.precond,
-                            stream=stream)
+                            predictor=args.predictor, tol_coarse=args.tol_coarse, stream=stream)
                for p in probs]
     units = sum(p.N * p.n_fine * m.ndof for p, m in zip(probs, members))
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -253,7 +256,7 @@ def run_batched(args, local):
         "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": "32 coax cables, seed 2026: nr 20-200, ntheta 40-400, 1-50 A, sigma 1e6-3e7, "
                                "N in {16,32,64}, 20-50 fine steps", "precision": args.precision,
-                   "precond": args.precond,
+                   "precond": args.precond, "predictor": args.predictor, "tol_coarse": args.tol_coarse,
                    "fine_dof_steps_per_step": units, "l2": "flushed between steps (512 MB write)"},
         "sequential_single_handles": {"value": seq_value, "unit": UNIT, "ms": seq_ms},
         "batched_over_sequential": value / seq_value,
@@ -471,7 +474,7 @@ def main():
     mixed = args.precision == "mixed"
     solver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
                           newton_schedule=bool(args.newton_schedule), precond=args.precond,
-                          tol_coarse=args.tol_coarse, stream=stream)
+                          tol_coarse=args.tol_coarse, predictor=args.predictor, stream=stream)
     ndof = solver.ndof
     units_per_step = prob.N * prob.n_fine * ndof
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
@@ -486,6 +489,7 @@ def main():
     solver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
     for _ in range(max(3, args.warmup)):
         solver.iterate()
+    U_start = solver.get_state()   # the timed steps and every e2e step start from here
 
     # ---- timed region: K iterations, L2 flushed between them
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -530,18 +534,23 @@ def main():
                 "kernel": "fine_sweep_kernel<double>", "hbm_gbs_equiv": pcg_bytes / fine_s / 1e9}
 
     # ---- end to end through the C ABI with host buffers
-    pinned = torch.zeros((prob.N, prob.mesh.n_nodes), dtype=torch.float64).pin_memory()
-    U_host = pinned.numpy()
-    U_host[:] = solver.get_state()
+    # every e2e step repeats the first timed step's work: the same input state
+    # (from pinned host memory) each time, the result read back to the host
+    pinned_in = torch.from_numpy(np.ascontiguousarray(U_start)).pin_memory()
+    pinned_out = torch.zeros_like(pinned_in).pin_memory()
+    U_in, U_out = pinned_in.numpy(), pinned_out.numpy()
     e2e_times = []
     for k in range(args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        solver.set_state(U_host)
+        solver.set_state(U_in)
         solver.iterate()
-        U_host[:] = solver.get_state()
+        U_out[:] = solver.get_state()
         e2e_times.append(time.perf_counter() - t0)
-    e2e_value = units_per_step * args.steps * world / sum(e2e_times)
+    e2e_units = units_per_step
+    e2e_value = e2e_units * args.steps * world / sum(e2e_times)
+    # the device-timed rate of that same first step, for comparison with e2e
+    first_step_value = units_per_step / (step_ms[0] * 1e-3)
     state_bytes = prob.N * prob.mesh.n_nodes * 8
 
     # ---- time to periodic steady state from U = 0
@@ -549,7 +558,7 @@ def main():
     if not args.no_tts:
         tsolver = from_problem(prob, precision=args.precision, coarse_at=args.coarse_at,
                                newton_schedule=bool(args.tts_schedule), precond=args.precond,
-                               tol_coarse=args.tol_coarse, stream=stream)
+                               tol_coarse=args.tol_coarse, predictor=args.predictor, stream=stream)
         tsolver.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -580,13 +589,14 @@ def main():
                                "sigma=2e7, Brauer steel, 10 A 50 Hz", "precision": args.precision,
                    "parallelism": "replicas only", "l2": "flushed between steps (512 MB write)",
                    "coarse_at": args.coarse_at, "newton_schedule": args.newton_schedule,
-                   "precond": args.precond, "tol_coarse": args.tol_coarse},
+                   "precond": args.precond, "tol_coarse": args.tol_coarse, "predictor": args.predictor},
         "time_to_steady_state": tts,
         "per_step": {"pcg_iters": pcg / args.steps, "newton_iters": newton / args.steps,
                      "fine_ms": sum(fine_ms) / args.steps, "step_ms": step_ms},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
+                "d2h_bytes_per_step": state_bytes, "repeats": "the first timed step (same input state) each time",
+                "device_rate_of_that_step": first_step_value},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

@@ -122,7 +122,8 @@ typedef struct pppc_config {
     void* alloc_ctx;      /* passed to alloc/free_fn */
     double eta0;          /* PCG forcing term of each step's first Newton iteration; later ones
                              follow Eisenstat-Walker, 0.9 (|R_k|/|R_k-1|)^2, within [tol_lin, 0.1] */
-    int32_t predictor;    /* 1: start each fine step's Newton from 2 u^m - u^{m-1} (default 1) */
+    int32_t predictor;    /* Newton start of each fine step: 0 u^m; 1 (default) 2 u^m - u^{m-1};
+                             2 3 u^m - 3 u^{m-1} + u^{m-2} (quadratic extrapolation) */
     int32_t method;       /* pppc_method (default PPPC_METHOD_PPPC) */
     int32_t coarse_at;    /* pppc_coarse_at: where the coarse stiffness is frozen (default U^k) */
     int32_t newton_schedule; /* 1: inexact PP-PC, the fine Newton tolerance of iteration k is

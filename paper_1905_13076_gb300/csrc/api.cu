@@ -197,6 +197,7 @@ FineArgs pppc::detail::fine_args(pppc_handle* h, double* Fout) {
     a.predictor = h->cfg.predictor;
     a.x = h->x;
     a.dx = h->dx;
+    a.uprev2 = h->uprev2;
     if (h->cfg.precond == 1) {
         a.tri = kTriChunk;
         a.tri_low = h->d_tri_low;
@@ -546,6 +547,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (c.coarse_at != PPPC_COARSE_AT_U && c.coarse_at != PPPC_COARSE_AT_F) why = "unknown coarse_at";
     else if (c.newton_schedule != 0 && c.newton_schedule != 1) why = "newton_schedule must be 0 or 1";
     else if (c.precond != 0 && c.precond != 1) why = "precond must be 0 or 1";
+    else if (c.predictor < 0 || c.predictor > 2) why = "predictor must be 0, 1 or 2";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
@@ -766,6 +768,8 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         if (!*v) return fail(h, PPPC_ERR_NOMEM, "workspace allocation failed");
         CK(cudaMemsetAsync(*v, 0, LV * ts, h->st));
     }
+    h->uprev2 = nullptr;
+    if (h->cfg.predictor == 2) TRY(alloc_n(h, &h->uprev2, LV));
     if (h->cfg.precond == 1) {
         std::vector<int> low(hm.ndof, -1);
         for (int i = 1; i < hm.ndof; ++i)

@@ -83,7 +83,8 @@ struct FineArgs {
     void* x;                 // [ndof*NB] of T: the Newton correction being solved for
     void* dx;                // [ndof*NB] of T: each lane's last accepted Newton step (for backtracking)
     double eta0;             // PCG forcing term of the first Newton iteration of a step
-    int predictor;           // 1: start each step's Newton from 2 u^m - u^{m-1}
+    int predictor;           // 1: start each step's Newton from 2 u^m - u^{m-1}; 2: 3 u^m - 3 u^{m-1} + u^{m-2}
+    double* uprev2;          // predictor 2: [ndof*NB] u^{m-2}
     void* J;                 // [n_slots*NB] of T
     void* invd_sp;           // [n_sp*NB] of T
     void* part;              // [2][gridDim][3 * NB] per-block partial sums of type T

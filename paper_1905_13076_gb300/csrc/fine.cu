@@ -703,16 +703,26 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
         // adjoint, u is lambda, u_prev = lambda_{m+1}, and level j counts down.
         const int j = a.adjoint ? a.n_fine - step : step;
         const bool extrap = !a.adjoint && a.predictor && step > 0;
+        const bool quad = a.predictor == 2 && !a.adjoint;   // keeps u^{m-2} in uprev2
         for (int i = row0; i < re; i += RB) {
             const size_t o = (size_t)i * NB + l0;
             const Lanes<double, V> um = ldv<double, V>(u + o);
             if (a.traj_out && step == 0) stv<double, V>(a.traj_out + o, um);
-            if (extrap) {
+            if (extrap || quad) {
                 const Lanes<double, V> uo = ldv<double, V>(uprev + o);
-                Lanes<double, V> un;
+                if (extrap) {
+                    Lanes<double, V> un;
+                    if (quad && step > 1) {
+                        const Lanes<double, V> uo2 = ldv<double, V>(a.uprev2 + o);
 #pragma unroll
-                for (int h = 0; h < V; ++h) un.v[h] = um.v[h] + (um.v[h] - uo.v[h]);
-                stv<double, V>(u + o, un);
+                        for (int h = 0; h < V; ++h) un.v[h] = 3.0 * (um.v[h] - uo.v[h]) + uo2.v[h];
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < V; ++h) un.v[h] = um.v[h] + (um.v[h] - uo.v[h]);
+                    }
+                    stv<double, V>(u + o, un);
+                }
+                if (quad) stv<double, V>(a.uprev2 + o, uo);
             }
             stv<double, V>(uprev + o, um);
         }

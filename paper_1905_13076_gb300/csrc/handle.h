@@ -61,6 +61,7 @@ struct pppc_handle {
     pppc_stats stats{};
     double rr_prev = INFINITY;   // rel_res of the previous iteration (inexact PP-PC schedule)
     int* d_tri_low = nullptr;    // tridiagonal-chunk preconditioner: CSR index of (i, i-1)
+    double* uprev2 = nullptr;    // quadratic predictor: u^{m-2}
     void *tri_m = nullptr, *tri_ie = nullptr;
     // per nonlinear element: its region; per region: sigma (for the adjoint)
     std::vector<int> nl_region;

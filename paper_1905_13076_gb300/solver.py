@@ -42,7 +42,7 @@ class PPPC:
     def __init__(self, T: float, N: int, n_fine: int, precision: str = "fp64",
                  coarse_lin: str = "avg_jacobian", tol_newton: float = 1e-10, max_newton: int = 30,
                  tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
-                 max_coarse: int = 20000, eta0: float = 1e-2, predictor: bool = True, method: str = "pppc",
+                 max_coarse: int = 20000, eta0: float = 1e-2, predictor: int = 1, method: str = "pppc",
                  coarse_at: str = "U", newton_schedule: bool = False, precond: str = "jacobi", stream=None):
         self._lib = _lib.load()
         cfg = pppc_config()
@@ -53,7 +53,7 @@ class PPPC:
         cfg.tol_newton, cfg.max_newton = float(tol_newton), int(max_newton)
         cfg.tol_lin, cfg.max_lin = float(tol_lin), int(max_lin)
         cfg.tol_coarse, cfg.max_coarse = float(tol_coarse), int(max_coarse)
-        cfg.eta0, cfg.predictor = float(eta0), int(bool(predictor))
+        cfg.eta0, cfg.predictor = float(eta0), int(predictor)
         cfg.method = _lib.METHODS[method]
         cfg.coarse_at = _lib.COARSE_AT[coarse_at]
         cfg.newton_schedule = int(bool(newton_schedule))

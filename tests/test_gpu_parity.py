@@ -345,3 +345,20 @@ def test_tridiagonal_chunk_preconditioner_matches_oracle(precision, tol):
         U = s.get_state()
     pp = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=40)
     assert rel(free(prob, U), pp.U) < tol
+
+
+def test_quadratic_predictor_matches_oracle():
+    """predictor = 2 starts each step's Newton from the quadratic
+    extrapolation: only the Newton path changes, not the steps' solutions."""
+    prob = workload("small")
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    ref = fine_sweep(m, free(prob, U0), prob.N, prob.n_fine, prob.T)
+    with gpu_solver(prob, predictor=2, tol_lin=1e-12) as s:
+        F = s.propagate_fine(U0)
+        n2 = s.stats()["newton_iters"]
+    with gpu_solver(prob, predictor=1, tol_lin=1e-12) as s:
+        s.propagate_fine(U0)
+        n1 = s.stats()["newton_iters"]
+    assert rel(free(prob, F), ref) < TOL64
+    assert n2 <= n1
