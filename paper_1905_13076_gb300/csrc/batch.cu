@@ -473,12 +473,17 @@ pppc_status pppc_batch_create(pppc_handle* const* members, int32_t count, int32_
     if (!out) return reject(PPPC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!members || count < 1) return reject(PPPC_ERR_INVALID_ARG, "members is NULL or count < 1");
+    // argument errors first (NULL or repeated members), then the members' state
+    for (int c = 0; c < count; ++c) {
+        const std::string who = "member " + std::to_string(c);
+        if (!members[c]) return reject(PPPC_ERR_INVALID_ARG, who + " is NULL");
+        for (int d = 0; d < c; ++d)
+            if (members[d] == members[c])
+                return reject(PPPC_ERR_INVALID_ARG, who + " repeats member " + std::to_string(d));
+    }
     for (int c = 0; c < count; ++c) {
         const pppc_handle* h = members[c];
         const std::string who = "member " + std::to_string(c);
-        if (!h) return reject(PPPC_ERR_INVALID_ARG, who + " is NULL");
-        for (int d = 0; d < c; ++d)
-            if (members[d] == h) return reject(PPPC_ERR_INVALID_ARG, who + " repeats member " + std::to_string(d));
         if (!h->has_mesh || !h->has_source) return reject(PPPC_ERR_STATE, who + " has no mesh or source");
         if (h->fp32 != members[0]->fp32) return reject(PPPC_ERR_UNSUPPORTED, who + ": precisions differ");
         if (h->st != members[0]->st) return reject(PPPC_ERR_UNSUPPORTED, who + ": streams differ");

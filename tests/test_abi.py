@@ -86,3 +86,51 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_config_options_are_validated(lib):
+    """Every option field of pppc_config is range-checked at create time (no
+    device work): method, coarse_at, newton_schedule, precond, predictor."""
+    from paper_1905_13076_gb300._lib import pppc_config
+
+    cases = [("method", 2, b"method"), ("coarse_at", 2, b"coarse_at"), ("newton_schedule", 2, b"newton_schedule"),
+             ("precond", 3, b"precond"), ("predictor", 3, b"predictor"), ("precision", 5, b"precision"),
+             ("coarse_lin", 7, b"coarse_lin"), ("eta0", 1.5, b"eta0")]
+    for field, bad, word in cases:
+        cfg = pppc_config()
+        lib.pppc_config_default(ctypes.byref(cfg))
+        setattr(cfg, field, bad)
+        h = ctypes.c_void_p()
+        assert lib.pppc_create(ctypes.byref(cfg), ctypes.byref(h)) == 1, field
+        assert h.value is None
+        assert word in lib.pppc_last_error(None), (field, lib.pppc_last_error(None))
+    cfg = pppc_config()
+    lib.pppc_config_default(ctypes.byref(cfg))
+    assert (cfg.method, cfg.coarse_at, cfg.newton_schedule, cfg.precond, cfg.predictor) == (0, 0, 0, 0, 1)
+    for field, good in [("method", 1), ("coarse_at", 1), ("newton_schedule", 1), ("precond", 1), ("predictor", 2)]:
+        c2 = pppc_config()
+        lib.pppc_config_default(ctypes.byref(c2))
+        setattr(c2, field, good)
+        h = ctypes.c_void_p()
+        assert lib.pppc_create(ctypes.byref(c2), ctypes.byref(h)) == 0, field
+        lib.pppc_destroy(h)
+
+
+def test_batch_and_adjoint_refuse_bad_arguments_without_a_device(lib):
+    """Argument checks of the batch and adjoint calls come before any device work."""
+    from paper_1905_13076_gb300._lib import pppc_adjoint_result, pppc_config
+
+    b = ctypes.c_void_p()
+    assert lib.pppc_batch_create(None, 0, 1, ctypes.byref(b)) == 1
+    assert b"count" in lib.pppc_batch_last_error(None)
+    cfg = pppc_config()
+    lib.pppc_config_default(ctypes.byref(cfg))
+    h = ctypes.c_void_p()
+    assert lib.pppc_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    arr = (ctypes.c_void_p * 1)(h.value)
+    assert lib.pppc_batch_create(arr, 1, 1, ctypes.byref(b)) == 3        # member without a mesh
+    arr2 = (ctypes.c_void_p * 2)(h.value, h.value)
+    assert lib.pppc_batch_create(arr2, 2, 1, ctypes.byref(b)) == 1       # the same member twice
+    res = pppc_adjoint_result()
+    assert lib.pppc_adjoint(h, 2, 1e-10, 10, ctypes.byref(res)) == 3     # no mesh yet
+    lib.pppc_destroy(h)
