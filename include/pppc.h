@@ -393,6 +393,17 @@ pppc_status pppc_batch_get_teams(pppc_batch* b, int32_t* fine_blocks, int32_t* c
 /* Last error on b, or of the last failed pppc_batch_create when b is NULL. */
 const char* pppc_batch_last_error(pppc_batch* b);
 
+/* The tuner's split, host only (no device work): blocks[count] for members
+ * with costs cost[count] (time x blocks, > 0), caps cap[count] (>= 1) and
+ * active[count] (0/1) over `total` blocks, minimising the largest
+ * cost / blocks: every active member gets one block, then each further block
+ * goes to the active member with the largest cost / blocks below its cap.
+ * Inactive members get 0.  *makespan (may be NULL) receives the largest
+ * cost / blocks.  Errors: INVALID_ARG (NULL array, count < 1, a cost <= 0
+ * or cap < 1 of an active member, fewer blocks than active members). */
+pppc_status pppc_batch_plan(const double* cost, const int32_t* cap, const int32_t* active, int32_t count,
+                            int32_t total, int32_t* blocks, double* makespan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -642,6 +642,25 @@ pppc_status pppc_batch_get_stats(pppc_batch* b, pppc_batch_stats* out) {
     return PPPC_OK;
 }
 
+pppc_status pppc_batch_plan(const double* cost, const int32_t* cap, const int32_t* active, int32_t count,
+                            int32_t total, int32_t* blocks, double* makespan) {
+    if (!cost || !cap || !active || !blocks || count < 1) return PPPC_ERR_INVALID_ARG;
+    std::vector<double> c(cost, cost + count);
+    std::vector<int> cp(cap, cap + count), out;
+    std::vector<char> act(count);
+    int n_active = 0;
+    for (int i = 0; i < count; ++i) {
+        act[i] = active[i] != 0;
+        if (act[i] && (!(c[i] > 0.0) || cp[i] < 1)) return PPPC_ERR_INVALID_ARG;
+        n_active += act[i];
+    }
+    if (total < n_active) return PPPC_ERR_INVALID_ARG;
+    const double mk = split_blocks(c, act, cp, total, out);
+    for (int i = 0; i < count; ++i) blocks[i] = out[i];
+    if (makespan) *makespan = mk;
+    return PPPC_OK;
+}
+
 pppc_status pppc_batch_get_teams(pppc_batch* b, int32_t* fine_blocks, int32_t* cocg_blocks) {
     if (!b) return PPPC_ERR_INVALID_ARG;
     for (int c = 0; c < b->count; ++c) {

@@ -134,3 +134,40 @@ def test_batch_and_adjoint_refuse_bad_arguments_without_a_device(lib):
     res = pppc_adjoint_result()
     assert lib.pppc_adjoint(h, 2, 1e-10, 10, ctypes.byref(res)) == 3     # no mesh yet
     lib.pppc_destroy(h)
+
+
+def test_batch_plan_minimises_the_slowest_team(lib):
+    """The tuner's greedy split equals the brute-force optimum of
+    max cost / blocks on small cases, respects caps and skips inactive
+    members (host-only call)."""
+    import itertools
+
+    import numpy as np
+
+    D, I = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    rng = np.random.default_rng(4)
+    for trial in range(60):
+        n = int(rng.integers(1, 5))
+        total = int(rng.integers(n, 9))
+        cost = rng.uniform(0.1, 10.0, n)
+        cap = rng.integers(1, 6, n).astype(np.int32)
+        active = (rng.uniform(size=n) < 0.8).astype(np.int32)
+        if not active.any():
+            active[0] = 1
+        blocks = np.zeros(n, dtype=np.int32)
+        mk = ctypes.c_double()
+        st = lib.pppc_batch_plan(cost.ctypes.data_as(D), cap.ctypes.data_as(I), active.ctypes.data_as(I), n, total,
+                                 blocks.ctypes.data_as(I), ctypes.byref(mk))
+        assert st == 0
+        act = active.astype(bool)
+        assert np.all(blocks[~act] == 0) and np.all(blocks[act] >= 1) and np.all(blocks <= np.maximum(cap, 0))
+        assert blocks.sum() <= total
+        best = np.inf
+        idx = np.nonzero(act)[0]
+        for combo in itertools.product(*[range(1, int(cap[i]) + 1) for i in idx]):
+            if sum(combo) <= total:
+                best = min(best, max(cost[i] / b for i, b in zip(idx, combo)))
+        assert mk.value == pytest.approx(best, rel=1e-12), (trial, blocks, mk.value, best)
+    one = np.ones(2, dtype=np.int32)
+    assert lib.pppc_batch_plan(np.ones(2).ctypes.data_as(D), one.ctypes.data_as(I), one.ctypes.data_as(I), 2, 1,
+                               np.zeros(2, dtype=np.int32).ctypes.data_as(I), None) == 1   # fewer blocks than members
