@@ -291,6 +291,17 @@ const char* pppc_last_error(pppc_handle* h);
 /* Static name of a status code. */
 const char* pppc_status_string(pppc_status s);
 
+/* ---- Failure detection self-test ------------------------------------------
+ * Every device-side wait of the library (grid barriers of the fine sweep and
+ * of the harmonic solves) gives up after 2 s of %globaltimer, sets a status
+ * word that the host maps to PPPC_ERR_TIMEOUT, and returns, so the context
+ * stays usable.  This call runs that path on purpose: one block waits, with
+ * the same bounded spin, on a device flag that nothing sets.  It returns
+ * PPPC_ERR_TIMEOUT after about 2 s (PPPC_ERR_CUDA if the launch fails) and
+ * synchronises `stream` (NULL = legacy default stream).  It allocates 8
+ * bytes of device memory and frees them. */
+pppc_status pppc_selftest_wait_timeout(void* stream);
+
 /* ---- Periodic adjoint: gradient of the eddy-current loss -------------------
  * Not in the paper; it reuses its method backwards in time.  For the periodic
  * state held by the handle (solve it first, e.g. pppc_solve_periodic to

@@ -362,3 +362,19 @@ def test_quadratic_predictor_matches_oracle():
         n1 = s.stats()["newton_iters"]
     assert rel(free(prob, F), ref) < TOL64
     assert n2 <= n1
+
+
+def test_device_wait_times_out_and_the_context_survives(library):
+    """A device wait on a flag that nothing sets runs out after the library's
+    2 s limit and reports PPPC_ERR_TIMEOUT; the context stays usable."""
+    import time
+
+    t0 = time.perf_counter()
+    st = library.pppc_selftest_wait_timeout(None)
+    dt = time.perf_counter() - t0
+    assert st == 8, library.pppc_status_string(st)       # PPPC_ERR_TIMEOUT
+    assert 1.5 < dt < 30.0
+    prob = workload("tiny")
+    with gpu_solver(prob) as s:
+        iters, rr = s.solve_periodic(tol=1e-10, kmax=40)
+    assert rr <= 1e-10
