@@ -3,7 +3,7 @@
 // All N subintervals march at once: lane n of every vector is subinterval
 // n+1, started from U_n at T_n.  Each implicit-Euler step of size dt solves
 //     R(u) = (M/dt)(u - u_prev) + K(u) u - I(t) g = 0
-// by Newton's method; each Newton correction solves J du = -R with Jacobi-
+// by Newton's method; each Newton correction solves J du = -R with
 // preconditioned conjugate gradients.  J = K_lin + M/dt + J_nl(u) is SPD; only
 // rows touching the nonlinear sheath (the "special" rows) differ per lane, so
 // their values are stored per lane and all other rows share one FP64 array.
@@ -27,6 +27,17 @@
 // and a thread owns V adjacent lanes of fixed rows for the whole launch, so
 // row-local data is only touched by its owner; other rows' data is read only
 // after a grid barrier.
+//
+// Options carried by FineArgs:
+// - preconditioner: Jacobi, or the tridiagonal part of every a.tri
+//   consecutive rows factorised per lane (tri_factor / tri_solve);
+// - Newton start: u^m, linear or quadratic extrapolation; lanes whose
+//   residual does not drop backtrack (apply_steps);
+// - a record of every fine level (traj_out), and an adjoint mode in which
+//   each lane runs the periodic adjoint of its subinterval backwards over
+//   that record (adjoint_rows);
+// - teams: fine_sweep_body runs on any team of blocks, the whole grid
+//   (fine_sweep_kernel) or one batch member's share (fine_batch_kernel).
 #include <cuda_runtime.h>
 
 #include <algorithm>
