@@ -616,14 +616,23 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         m[6] = q.is_source ? 1.0 : 0.0;
         m[7] = q.bmax > 0.0 ? q.bmax * q.bmax : INFINITY;   // cap on b = |B|^2
     }
+    // host-side validation and preprocessing first: an invalid mesh is
+    // refused before any device work and leaves the previous mesh in place
+    std::string err;
+    HostMesh hm_new;
+    if (!build_host_mesh(n_nodes, n_tri, tri, region, dirichlet, n_regions, kinds.data(), hm_new, err))
+        return fail(h, PPPC_ERR_INVALID_ARG, err);
+    {
+        bool any_source = false;
+        for (int e = 0; e < n_tri && !any_source; ++e) any_source = (hm_new.elem_kind[e] & ELEM_SOURCE) != 0;
+        if (!any_source) return fail(h, PPPC_ERR_INVALID_ARG, "no triangle lies in a source region");
+    }
     free_all(h);
     h->has_source = false;
     h->trace_cap = 0;
     for (auto& e : h->ev)
         if (!e) CK(cudaEventCreate(&e));
-    std::string err;
-    if (!build_host_mesh(n_nodes, n_tri, tri, region, dirichlet, n_regions, kinds.data(), h->hm, err))
-        return fail(h, PPPC_ERR_INVALID_ARG, err);
+    h->hm = std::move(hm_new);
     HostMesh& hm = h->hm;
     h->traj = h->lam = h->adjA = h->adjB = h->adjF = h->gpart = h->gout = nullptr;
     h->nl_sel = nullptr;
@@ -632,9 +641,6 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     h->region_sigma.resize(n_regions);
     h->region_kind = kinds;
     for (int r = 0; r < n_regions; ++r) h->region_sigma[r] = mat[r].sigma;
-    bool any_source = false;
-    for (int e = 0; e < n_tri && !any_source; ++e) any_source = (hm.elem_kind[e] & ELEM_SOURCE) != 0;
-    if (!any_source) return fail(h, PPPC_ERR_INVALID_ARG, "no triangle lies in a source region");
 
     // uploads
     std::vector<double> vxy(xy, xy + 2 * (size_t)n_nodes);

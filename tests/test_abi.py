@@ -171,3 +171,43 @@ def test_batch_plan_minimises_the_slowest_team(lib):
     one = np.ones(2, dtype=np.int32)
     assert lib.pppc_batch_plan(np.ones(2).ctypes.data_as(D), one.ctypes.data_as(I), one.ctypes.data_as(I), 2, 1,
                                np.zeros(2, dtype=np.int32).ctypes.data_as(I), None) == 1   # fewer blocks than members
+
+
+def test_invalid_meshes_are_refused_before_device_work(lib):
+    """set_mesh validates indices, regions, materials and the source on the
+    host: each of these inputs is refused with INVALID_ARG (no GPU needed)."""
+    import numpy as np
+
+    from paper_1905_13076_gb300._lib import pppc_config, pppc_material
+
+    cfg = pppc_config()
+    lib.pppc_config_default(ctypes.byref(cfg))
+    h = ctypes.c_void_p()
+    assert lib.pppc_create(ctypes.byref(cfg), ctypes.byref(h)) == 0
+    xy = np.array([[0, 0], [1, 0], [0, 1], [1, 1]], dtype=np.float64)
+    tri = np.array([[0, 1, 2], [1, 3, 2]], dtype=np.int32)
+    region = np.array([0, 0], dtype=np.int32)
+    dirichlet = np.array([0, 0, 0, 1], dtype=np.uint8)
+    mats = (pppc_material * 1)()
+    mats[0].nu_model, mats[0].nu, mats[0].is_source = 0, 1.0, 1
+
+    def set_mesh(t=tri, reg=region, m=mats, nreg=1):
+        return lib.pppc_set_mesh(h, 4, xy.ctypes.data, t.shape[0], t.ctypes.data, reg.ctypes.data,
+                                 dirichlet.ctypes.data, nreg, m)
+
+    bad_tri = tri.copy()
+    bad_tri[1, 2] = 7                                         # node index out of range
+    assert set_mesh(t=bad_tri) == 1
+    bad_reg = np.array([0, 3], dtype=np.int32)                # region index out of range
+    assert set_mesh(reg=bad_reg) == 1
+    m2 = (pppc_material * 1)()
+    m2[0].nu_model, m2[0].nu, m2[0].is_source = 0, -1.0, 1    # negative reluctivity
+    assert set_mesh(m=m2) == 1
+    m3 = (pppc_material * 1)()
+    m3[0].nu_model, m3[0].nu, m3[0].is_source = 0, 1.0, 0     # no source region
+    assert set_mesh(m=m3) == 1
+    m4 = (pppc_material * 1)()
+    m4[0].nu_model, m4[0].k1, m4[0].k2, m4[0].k3, m4[0].bmax, m4[0].is_source = 1, 3.8, 2.17, 396.2, -1.0, 1
+    assert set_mesh(m=m4) == 1                                # negative Brauer cap
+    assert lib.pppc_ndof(h) == 0                              # nothing was set up
+    lib.pppc_destroy(h)
