@@ -60,14 +60,23 @@ def test_conductivity_and_current_are_conserved(params):
 
 
 @settings(max_examples=10, deadline=None)
-@given(meshes, st.floats(0.3, 4.0))
+@given(meshes, st.floats(0.3, 2.5))
 def test_jacobian_matches_central_differences(params, tesla):
+    # below the 3 T cap of the Brauer law: there nu is smooth, and central
+    # differences are second-order accurate (across the cap the law is only
+    # C^1; test_oracle_fem checks a state wholly above it)
     m = model_of(params)
     u = smooth_state(m, tesla, params[2] + 1)
     v = np.random.default_rng(params[2]).standard_normal(m.ndof) * 1e-6
-    h = 1e-2
-    fd = (m.Ku(u + h * v) - m.Ku(u - h * v)) / (2 * h)
-    assert np.linalg.norm(fd - m.jacobian_K(u) @ v) <= 1e-6 * np.linalg.norm(fd)
+    Jv = m.jacobian_K(u) @ v
+    errs = []
+    for h in (1e-2, 1e-3):
+        fd = (m.Ku(u + h * v) - m.Ku(u - h * v)) / (2 * h)
+        errs.append(np.linalg.norm(fd - Jv) / np.linalg.norm(fd))
+    # second-order convergence of the difference quotient to J v (coarse
+    # jittered meshes reach the steep part of the law, so no fixed h fits all)
+    assert errs[1] < 1e-6
+    assert errs[1] < errs[0] / 30.0 or errs[1] < 1e-8   # or already at the rounding floor
 
 
 @settings(max_examples=5, deadline=None)
