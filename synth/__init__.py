@@ -12,6 +12,7 @@ meshes generated here stand in for it.
 """
 
 from .coax import (  # noqa: F401
+    BRAUER_BMAX,
     BRAUER_STEEL,
     NU0,
     RADII,
