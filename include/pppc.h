@@ -317,9 +317,9 @@ pppc_status pppc_selftest_wait_timeout(void* stream);
  * multi-harmonic coarse solve (Eq. 4, Eqs. 11-14) run backwards.  Its fine
  * propagators are the fine sweep's kernel in adjoint mode (each level an
  * iteratively refined PCG solve with the handle's preconditioner), with the
- * Jacobians J_m taken at the
- * forward trajectory, which one forward fine sweep from the state recomputes
- * at the start of the call.  Kbar is the forward's.
+ * Jacobians J_m taken at the forward trajectory, which one forward fine
+ * sweep from the state recomputes at the start of the call.  Kbar is the
+ * forward's.
  *     dP/dsigma_r = P_r / sigma_r - sum_m lam_m^T (M_r / sigma_r) du^m / dt,
  *     dP/dk_i     = - sum_m lam_m^T d(K(u^m) u^m)/dk_i.
  * tol and kmax bound the adjoint PP-PC (rel_res of the adjoint jumps).
