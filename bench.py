@@ -419,7 +419,8 @@ def cpu_baseline_pool(name, cores=None):
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(cores) as pool:
-            res = pool.map(_oracle_subinterval, [(name, n) for n in range(1, cores + 1)], chunksize=1)
+            res = pool.map_async(_oracle_subinterval, [(name, n) for n in range(1, cores + 1)],
+                                 chunksize=1).get(timeout=600)
     finally:
         for k, v in saved.items():
             if v is None:
