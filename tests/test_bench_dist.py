@@ -47,3 +47,32 @@ def test_aggregate_single_process():
 
     value, t_max = bench.aggregate(50.0, units_per_step=10.0, steps=4)
     assert t_max == 50.0 and value == pytest.approx(10.0 * 4 / 0.05)
+
+
+def test_clock_summary_reports_median_clock_and_active_reasons():
+    """The timing rules reject runs that saw thermal or hardware slowdown:
+    the sampler must report every reason that was active in any sample and
+    the median SM clock under load."""
+    import bench
+
+    s = bench.ClockSampler(0)
+    s.lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2050, 2070, 1399.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1400.2, 0x0000000000000008, Active, Not Active, Not Active, Active",
+        "garbage line",
+    ]
+    out = s.summary()
+    assert out["sm_mhz"] == 2050 and out["sm_max_mhz"] == 2070 and out["samples"] == 3
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    s.lines = []
+    assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_pcg_bytes_model_counts_the_tridiagonal_extras():
+    import bench
+
+    jac = bench.pcg_bytes_per_row_lane(True, 0.13, 6.9, 64)
+    tri = bench.pcg_bytes_per_row_lane(True, 0.13, 6.9, 64, tri=True)
+    assert 60 < jac < 90 and tri > jac
+    assert bench.pcg_bytes_per_row_lane(False, 0.13, 6.9, 64) > jac      # FP64 vectors
