@@ -89,3 +89,19 @@ def test_periodic_solution_is_half_wave_antisymmetric(params):
     traj = bruteforce_periodic(m, prob.N, prob.n_fine, prob.T, tol=1e-11)
     L = traj.shape[0] - 1
     assert np.linalg.norm(traj[L // 2:L] + traj[:L // 2]) <= 1e-8 * np.linalg.norm(traj)
+
+
+@settings(max_examples=4, deadline=None)
+@given(st.integers(5, 6), st.integers(6, 9), st.integers(0, 10_000), st.floats(1e6, 3e7), st.floats(2.0, 30.0))
+def test_pppc_fixed_point_is_the_periodic_solution(nr, nth, seed, sigma, amp):
+    """On random small cables PP-PC (Eq. 4, multi-harmonic coarse solve)
+    converges to the periodic solution found by Newton on all levels at once."""
+    from oracle.pppc import pppc
+
+    prob = make_problem("prop", nr, nth, 4, 2, sigma, amp=(amp,), seed=seed)
+    m = FEModel(prob)
+    ref = bruteforce_periodic(m, prob.N, prob.n_fine, prob.T, tol=1e-12, max_newton=80)
+    res = pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-11, kmax=80)
+    assert res.converged
+    U_ref = ref[0:prob.N * prob.n_fine:prob.n_fine]          # coarse points u^{n n_fine}
+    assert np.linalg.norm(res.U - U_ref) <= 1e-8 * np.linalg.norm(U_ref)
