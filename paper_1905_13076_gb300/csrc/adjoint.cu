@@ -151,20 +151,6 @@ int grid_of(long long n) {
     return (int)std::max(1LL, std::min(b, 65535LL));
 }
 
-#define CK(call)                                                                              \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return fail(h, e_ == cudaErrorMemoryAllocation ? PPPC_ERR_NOMEM : PPPC_ERR_CUDA, \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
-    } while (0)
-
-#define TRY(expr)                      \
-    do {                               \
-        pppc_status s_ = (expr);       \
-        if (s_ != PPPC_OK) return s_;  \
-    } while (0)
-
 pppc_status take(pppc_handle* h, double** p, size_t n) {
     void* ptr = nullptr;
     if (h->cfg.alloc) {

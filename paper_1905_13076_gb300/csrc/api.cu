@@ -60,20 +60,6 @@ pppc_status pppc::detail::fail(pppc_handle* h, pppc_status s, const std::string&
 
 namespace {
 
-#define CK(call)                                                                              \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return fail(h, e_ == cudaErrorMemoryAllocation ? PPPC_ERR_NOMEM : PPPC_ERR_CUDA, \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
-    } while (0)
-
-#define TRY(expr)                      \
-    do {                               \
-        pppc_status s_ = (expr);       \
-        if (s_ != PPPC_OK) return s_;  \
-    } while (0)
-
 void* dev_alloc(pppc_handle* h, size_t bytes) {
     if (bytes == 0) bytes = 16;
     void* ptr = nullptr;

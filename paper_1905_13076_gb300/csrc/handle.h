@@ -111,3 +111,20 @@ void choose_vec_rows(bool fp32, int NB, int rows_max, size_t budget, int* vec_ro
 
 }  // namespace detail
 }  // namespace pppc
+
+// Error plumbing of the handle-based calls: a failing CUDA call records its
+// text on h and returns PPPC_ERR_CUDA (PPPC_ERR_NOMEM for allocations); a
+// failing stage returns its status.  Both expect a pppc_handle* h in scope.
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? PPPC_ERR_NOMEM : PPPC_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define TRY(expr)                      \
+    do {                               \
+        pppc_status s_ = (expr);       \
+        if (s_ != PPPC_OK) return s_;  \
+    } while (0)
