@@ -211,3 +211,26 @@ def test_invalid_meshes_are_refused_before_device_work(lib):
     assert set_mesh(m=m4) == 1                                # negative Brauer cap
     assert lib.pppc_ndof(h) == 0                              # nothing was set up
     lib.pppc_destroy(h)
+
+
+def test_python_layer_raises_the_library_status(lib):
+    """The binding marshals arguments only: an error status of the C call
+    comes back as PPPCError with that status and the library's message."""
+    from paper_1905_13076_gb300 import PPPC, PPPCBatch, PPPCError
+
+    s = PPPC(0.02, 16, 20)                              # creating a handle needs no device
+    with pytest.raises(PPPCError) as e:
+        s.iterate()
+    assert e.value.status == 3 and "set_mesh" in e.value.message
+    with pytest.raises(PPPCError) as e:
+        s.adjoint(2)
+    assert e.value.status == 3
+    with pytest.raises(PPPCError) as e:
+        PPPCBatch([s])
+    assert e.value.status == 3 and "member 0" in e.value.message
+    with pytest.raises(PPPCError) as e:
+        PPPC(0.02, 15, 20)                              # odd N
+    assert e.value.status == 1
+    with pytest.raises(KeyError):
+        PPPC(0.02, 16, 20, precond="ilu")               # unknown option names fail in Python
+    s.close()
