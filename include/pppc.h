@@ -232,7 +232,11 @@ pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_
  * system (K + (1 - exp(-i 2 pi p / N)) C) x_p = b_p with the same batched
  * Jacobi-preconditioned COCG kernel as the coarse solve of pppc_iterate.
  * K and C are real n x n matrices on one CSR pattern (rowptr[n+1], col[nnz],
- * kval[nnz], cval[nnz]; every row must hold its diagonal entry).  b and x are
+ * kval[nnz], cval[nnz] with nnz = rowptr[n]; rowptr[0] = 0, rowptr never
+ * decreases, every col entry lies in [0, n) and every row holds its diagonal
+ * entry).  The pattern is checked on the device before the solve: rowptr
+ * first, and col only once rowptr has passed, so a bad pattern returns
+ * PPPC_ERR_INVALID_ARG without any out-of-range access.  b and x are
  * complex, interleaved (re, im), laid out [n][N/2+1].  All pointers are
  * device memory owned by the caller; the call stops when
  * ||r_p|| <= tol ||b_p|| for every p or after max_it iterations, writes the
@@ -243,8 +247,7 @@ pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_
  * PPPC_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
  * the process exits.  Limits: N even, 2 <= N <= PPPC_NOALLOC_MAX_N, and
  * n * (N/2 + 1) <= PPPC_NOALLOC_MAX_UNKNOWNS; larger requests return
- * PPPC_ERR_INVALID_ARG before any device work, as does a row without a
- * diagonal entry.  The first call on each device looks up the array's device
+ * PPPC_ERR_INVALID_ARG before any device work.  The first call on each device looks up the array's device
  * address (with that device current); make that first call before any stream
  * capture.  Every call shares the array and clears what must start at zero;
  * calls that overlap on the GPU (other streams or host threads on the same
@@ -301,6 +304,13 @@ const char* pppc_status_string(pppc_status s);
  * synchronises `stream` (NULL = legacy default stream).  It allocates 8
  * bytes of device memory and frees them. */
 pppc_status pppc_selftest_wait_timeout(void* stream);
+
+/* Target of the device code this library was built with, as the CUDA
+ * runtime reports it for the library's kernels (cudaFuncGetAttributes,
+ * binaryVersion = 10 major + minor; 103 for GB300's sm_103a).  Needs a
+ * device; no device work.  Errors: INVALID_ARG (out NULL), CUDA (no device,
+ * or no kernel image for it). */
+pppc_status pppc_binary_version(int32_t* out);
 
 /* ---- Periodic adjoint: gradient of the eddy-current loss -------------------
  * Not in the paper; it reuses its method backwards in time.  For the periodic

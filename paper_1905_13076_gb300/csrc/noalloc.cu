@@ -38,6 +38,20 @@ std::mutex g_scratch_mu;
 
 inline size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
+// Pass 1 over the caller's pattern: rowptr must start at 0 and never
+// decrease.  Only rowptr[0..n] is read.  Until this has passed, the row
+// ranges cannot be trusted to stay inside col[], so nothing reads col.
+__global__ void noalloc_check_rowptr_kernel(int n, const int* rowptr, int* status) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int a = rowptr[i], b = rowptr[i + 1];
+        if ((i == 0 && a != 0) || b < a) atomicCAS(status, 0, 1);
+    }
+}
+
+// Pass 2, once rowptr is known to be valid: every column index must lie in
+// [0, n) and every row must hold its diagonal.  An out-of-range index is
+// only compared, never used to address memory.
 __global__ void noalloc_setup_kernel(int n, int N, const int* rowptr, const int* col, int* row_slot,
                                      int* sp_index, int* diag_k, double* tw, int* status) {
     const int stride = gridDim.x * blockDim.x;
@@ -45,9 +59,13 @@ __global__ void noalloc_setup_kernel(int n, int N, const int* rowptr, const int*
         row_slot[i] = rowptr[i];
         sp_index[i] = i;
         int dk = -1;
-        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
-            if (col[k] == i) dk = k;
-        if (dk < 0) {
+        bool ok = true;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const int c = col[k];
+            if (c < 0 || c >= n) ok = false;
+            if (c == i) dk = k;
+        }
+        if (dk < 0 || !ok) {
             atomicCAS(status, 0, 1);
             dk = rowptr[i];  // never used: the host stops on the status
         }
@@ -125,14 +143,22 @@ extern "C" pppc_status pppc_harmonic_solve_noalloc(int32_t n, const int32_t* row
         cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
         cudaMemsetAsync(counters, 0, 3 * sizeof(long long), st) != cudaSuccess)
         return PPPC_ERR_CUDA;
-    noalloc_setup_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(
-        n, N, rowptr, col, row_slot, sp_index, diag_k, tw, status);
-    if (cudaGetLastError() != cudaSuccess) return PPPC_ERR_CUDA;
+    // validate the caller's pattern in two passes (rowptr, then col), each
+    // read back before anything depends on it
+    const int vblocks = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
     int code = 0;
+    noalloc_check_rowptr_kernel<<<vblocks, 256, 0, st>>>(n, rowptr, status);
+    if (cudaGetLastError() != cudaSuccess) return PPPC_ERR_CUDA;
     if (cudaMemcpyAsync(&code, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return PPPC_ERR_CUDA;
-    if (code != 0) return PPPC_ERR_INVALID_ARG;  // a row without a diagonal entry
+    if (code != 0) return PPPC_ERR_INVALID_ARG;  // rowptr does not start at 0 or decreases
+    noalloc_setup_kernel<<<vblocks, 256, 0, st>>>(n, N, rowptr, col, row_slot, sp_index, diag_k, tw, status);
+    if (cudaGetLastError() != cudaSuccess) return PPPC_ERR_CUDA;
+    if (cudaMemcpyAsync(&code, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PPPC_ERR_CUDA;
+    if (code != 0) return PPPC_ERR_INVALID_ARG;  // a column outside [0, n) or a row without its diagonal
 
     // every row is "special": its values are kval + c_p * cval, slot = CSR index
     CocgArgs a{};

@@ -114,3 +114,69 @@ def test_noalloc_rejects_oversized_requests(lib):
     st = lib.pppc_harmonic_solve_noalloc(4, idx.data_ptr(), idx.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
                                          512, dummy.data_ptr(), dummy.data_ptr(), 1e-10, 100, None, None)
     assert st == 1                                       # N above PPPC_NOALLOC_MAX_N
+
+
+def _tiny_system(dev):
+    """A 4 x 4 tridiagonal K and C on one CSR pattern (10 entries), and a
+    right-hand side for N = 2 (two harmonics)."""
+    import torch
+
+    rowptr = np.array([0, 2, 5, 8, 10], dtype=np.int32)
+    col = np.array([0, 1, 0, 1, 2, 1, 2, 3, 2, 3], dtype=np.int32)
+    kval = np.where(np.repeat(np.arange(4), np.diff(rowptr)) == col, 4.0, -1.0)
+    cval = np.where(np.repeat(np.arange(4), np.diff(rowptr)) == col, 2.0, 0.5)
+    b = np.zeros((4, 2 * 2))
+    b[:, 0] = [1.0, -2.0, 0.5, 3.0]          # p = 0, real part
+    b[:, 2] = [0.25, 1.0, -1.0, 2.0]         # p = 1, real part
+    t = {k: torch.from_numpy(v).to(dev) for k, v in
+         dict(rowptr=rowptr, col=col, kval=kval, cval=cval, b=b).items()}
+    t["x"] = torch.zeros(4, 4, dtype=torch.float64, device=dev)
+    return t
+
+
+def _call(lib, t, n=4, tol=1e-12, max_it=100):
+    its = ctypes.c_int32(-1)
+    st = lib.pppc_harmonic_solve_noalloc(n, t["rowptr"].data_ptr(), t["col"].data_ptr(), t["kval"].data_ptr(),
+                                         t["cval"].data_ptr(), 2, t["b"].data_ptr(), t["x"].data_ptr(), tol, max_it,
+                                         None, ctypes.byref(its))
+    return st, its.value
+
+
+def test_noalloc_rejects_invalid_patterns_without_reading_out_of_range(lib):
+    """The caller's CSR pattern is validated before the solve: a rowptr that
+    does not start at 0 or decreases (col is then never read), a column
+    index outside [0, n), and a row without its diagonal all return
+    PPPC_ERR_INVALID_ARG.  Every buffer here is in bounds."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    t = _tiny_system(dev)
+    assert _call(lib, t)[0] == 0                          # the valid pattern solves
+    cases = {
+        "rowptr does not start at 0": ("rowptr", 0, 1),
+        "rowptr decreases": ("rowptr", 2, 1),
+        "column index past n": ("col", 4, 7),
+        "negative column index": ("col", 3, -1),
+        "row 2 without its diagonal": ("col", 6, 0),
+    }
+    for why, (name, pos, val) in cases.items():
+        bad = {k: v.clone() for k, v in t.items()}
+        bad[name][pos] = val
+        st, _ = _call(lib, bad)
+        assert st == 1, (why, lib.pppc_status_string(st))
+    # the shared scratch array is still usable after rejected calls
+    st, its = _call(lib, t)
+    assert st == 0 and its > 0
+
+
+def test_noalloc_reports_the_iteration_cap(lib):
+    """A solvable system stopped after one iteration at a tolerance it cannot
+    reach returns PPPC_ERR_LINEAR."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    t = _tiny_system(dev)
+    st, _ = _call(lib, t, tol=1e-14, max_it=1)
+    assert st == 5, lib.pppc_status_string(st)            # PPPC_ERR_LINEAR
+    st, its = _call(lib, t, tol=1e-12, max_it=100)
+    assert st == 0 and 1 < its <= 100
