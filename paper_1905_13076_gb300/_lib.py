@@ -100,6 +100,7 @@ SIGNATURES = {
     "pppc_harmonic_solve_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                               c_void_p, c_void_p, c_double, c_int32, c_void_p, _IPTR]),
     "pppc_selftest_wait_timeout": (c_int32, [c_void_p]),
+    "pppc_binary_version": (c_int32, [_IPTR]),
     "pppc_adjoint": (c_int32, [c_void_p, c_int32, c_double, c_int32, POINTER(pppc_adjoint_result)]),
     "pppc_batch_create": (c_int32, [POINTER(c_void_p), c_int32, c_int32, POINTER(c_void_p)]),
     "pppc_batch_destroy": (None, [c_void_p]),

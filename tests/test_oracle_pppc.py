@@ -10,7 +10,7 @@ import scipy.sparse.linalg as spla
 from oracle.fem import FEModel
 from oracle.periodic import bruteforce_periodic, linear_periodic_phasor
 from oracle.pppc import (block_cyclic_matrix, coarse_matrices, coarse_step, coarse_update,
-                         parareal_ivp, ppic, pppc, solve_block_cyclic, solve_multiharmonic)
+                         parareal_ivp, ppic, ppic_update, pppc, solve_block_cyclic, solve_multiharmonic)
 from oracle.stepping import fine_sweep, one_period
 from synth import workload
 
@@ -177,3 +177,40 @@ def test_jump_of_zero_state_is_the_fine_sweep(tiny):
     assert np.all(np.linalg.norm(F, axis=1) > 0)
     # half-wave symmetry of the first sweep: F_{n+N/2}(0) = -F_n(0)
     assert rel(F[p.N // 2:], -F[:p.N // 2]) < 1e-10
+
+
+def test_ppic_sweep_is_ivp_parareal_with_the_relaxed_start(tiny):
+    """Eq. 5: a PP-IC sweep is one initial-value Parareal iteration whose
+    start value is the previous end-of-period value U_N^k.  Started from an
+    IVP-Parareal iterate U^0 (the coarse sweep from u0) whose end value is
+    set to u0, one ppic_update must reproduce the next IVP-Parareal iterate
+    U^1 (pinned above by its exactness for n <= k).  A wrong sign, index or
+    start value in the sweep's correction term breaks the equality."""
+    p, m = tiny
+    u0 = knee_states(m, 1, 9)[0]
+    its = parareal_ivp(m, u0, p.N, p.n_fine, p.T, iterations=1)
+    U = its[0].copy()
+    U[p.N] = u0                                          # relaxed start: U_0^{k+1} = U_N^k = u0
+    F = fine_sweep(m, U[:p.N], p.N, p.n_fine, p.T)
+    new = ppic_update(m, U, F, p.N, p.T)
+    assert np.allclose(new[0], u0, rtol=0, atol=0)
+    assert rel(new, its[1]) < 1e-13
+    # the end value does move: the check is not vacuous
+    assert rel(new[p.N], U[p.N]) > 1e-3
+
+
+def test_ppic_with_coarse_equal_to_fine_is_sequential_stepping():
+    """Linear material and one fine step per subinterval: the coarse step of
+    Eq. 8 is the fine step, so every PP-IC sweep (Eq. 5) reduces to one
+    period of sequential implicit Euler from the previous end value, and
+    after k sweeps from rest U_N^k is the state after k periods."""
+    p = workload("tiny", linear_sheath=True, n_fine=1)
+    m = FEModel(p)
+    U = np.zeros((p.N + 1, m.ndof))
+    u = np.zeros(m.ndof)
+    for k in range(3):
+        F = fine_sweep(m, U[:p.N], p.N, p.n_fine, p.T, tol_newton=1e-13)
+        U = ppic_update(m, U, F, p.N, p.T)
+        traj = one_period(m, u, p.N, p.n_fine, p.T, tol_newton=1e-13)
+        assert rel(U, traj) < 1e-10, k
+        u = traj[-1]
