@@ -133,6 +133,20 @@ typedef struct pppc_config {
     int32_t precond;      /* fine PCG preconditioner: 0 Jacobi (default); 1 the tridiagonal part of
                              every 4 consecutive rows, factorised per lane (row order should follow
                              the mesh's strongest couplings, e.g. the rings of a polar mesh) */
+    int32_t lane_team;    /* how the N subintervals of a fine sweep share the GPU.  The sweep's
+                             lanes are independent, so they run as teams of lane_team lanes, each
+                             team on its own share of the SMs with its own barriers and
+                             reductions, never waiting for another team.
+                             0 (default): chosen by measurement at the handle's first sweep --
+                               every candidate V 2^i (V = 4 lanes in PPPC_MIXED, 2 in PPPC_FP64)
+                               dividing the padded N is timed on the sweep's first fine level,
+                               and the fastest is kept for every handle of the process with the
+                               same precision, padded N, preconditioner and floor(log2 ndof);
+                             > 0: that many lanes per team (one of the candidates, else
+                               INVALID_ARG from pppc_set_mesh);
+                             -1: one team over all lanes.
+                             Results agree to rounding whatever the choice; they are bitwise
+                             reproducible for a fixed choice. */
 } pppc_config;
 
 /* Iteration counts of the most recent iterate / solve / propagate call. */
@@ -148,6 +162,11 @@ typedef struct pppc_stats {
     int64_t launches;        /* kernels this library launched during the call */
     int64_t backtracks;      /* Newton rounds of the fine sweeps in which some lane halved its step
                                 because the residual did not drop (0 on well-behaved problems) */
+    int64_t pcg_lane_rounds; /* sum over lane teams of PCG rounds x lanes per team: the lane
+                                vectors the PCG iterations streamed */
+    int64_t pcg_lane_iters;  /* sum over subintervals of the PCG iterations each one needed;
+                                1 - pcg_lane_iters / pcg_lane_rounds is the lockstep idle share */
+    int64_t newton_lane_rounds; /* sum over lane teams of Newton rounds x lanes per team */
 } pppc_stats;
 
 /* Fill *cfg with defaults: T=0.02, N=16, n_fine=20, FP64, averaged Jacobian,
@@ -197,6 +216,18 @@ pppc_status pppc_get_state(pppc_handle* h, double* U, int32_t on_device);
  * U and F use the state layout; they may not alias.  Does not change the
  * handle's state.  Errors: NEWTON, LINEAR, BREAKDOWN, NAN, TIMEOUT, CUDA. */
 pppc_status pppc_propagate_fine(pppc_handle* h, const double* U, double* F, int32_t on_device);
+
+/* A window of the fine sweep (Eq. 3 on part of each subinterval): every
+ * subinterval j+1 marches `count` implicit-Euler steps from its fine level
+ * `first`, i.e. U[j] is the state at t = T_j + first dt and F[j] receives the
+ * state at T_j + (first + count) dt, with dt = T / (N n_fine) as in
+ * pppc_propagate_fine.  Windows [0, a), [a, b), ..., [c, n_fine) chained
+ * through F reproduce pppc_propagate_fine up to the Newton tolerance (each
+ * window starts its first step's Newton from u itself, not from an
+ * extrapolation).  Layout, aliasing and errors as pppc_propagate_fine, plus
+ * INVALID_ARG unless 0 <= first, 1 <= count and first + count <= n_fine. */
+pppc_status pppc_propagate_fine_window(pppc_handle* h, const double* U, double* F, int32_t first, int32_t count,
+                                       int32_t on_device);
 
 /* The coarse part of one PP-PC iteration (Eq. 4 with the implicit-Euler
  * coarse propagator of Eq. 8, solved through Eqs. 9-14): given U^k and the
@@ -261,8 +292,24 @@ pppc_status pppc_harmonic_solve_noalloc(int32_t n, const int32_t* rowptr, const 
                                         const double* b, double* x, double tol, int32_t max_it,
                                         void* stream, int32_t* iters_out);
 
-/* Iteration counts of the last propagate / coarse / iterate / solve call. */
+/* Iteration counts of the last propagate / coarse / iterate / solve call.
+ * newton_iters and pcg_iters are lockstep rounds: per fine sweep the largest
+ * count over the lane teams (the sweep's critical path), summed over sweeps. */
 pppc_status pppc_get_stats(pppc_handle* h, pppc_stats* out);
+
+/* The lane-team split of the fine sweep in use (pppc_config.lane_team) and
+ * what the tuner measured for each candidate. */
+typedef struct pppc_fine_plan_info {
+    int32_t lanes_per_team;     /* 0: not chosen yet (before the first sweep); -1: one team */
+    int32_t teams;
+    int32_t threads_per_row;    /* lanes_per_team / lanes per thread (4 FP32, 2 FP64) */
+    int32_t blocks_min, blocks_max;  /* blocks (one per SM) per team */
+    int32_t n_candidates;
+    int32_t candidate_lanes[16];
+    double candidate_ms[16];    /* device time of one fine level per candidate, 0 if not timed
+                                   by this handle (its bucket had been tuned before) */
+} pppc_fine_plan_info;
+pppc_status pppc_get_fine_plan(pppc_handle* h, pppc_fine_plan_info* out);
 
 /* Newton trace of the fine propagators (diagnostics).  pppc_set_trace(h, cap)
  * with cap > 0 makes every later fine sweep record up to cap records of

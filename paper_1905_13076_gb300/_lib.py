@@ -39,6 +39,7 @@ class pppc_config(ctypes.Structure):
         ("max_coarse", c_int32), ("stream", c_void_p), ("alloc", c_void_p),
         ("free_fn", c_void_p), ("alloc_ctx", c_void_p), ("eta0", c_double), ("predictor", c_int32),
         ("method", c_int32), ("coarse_at", c_int32), ("newton_schedule", c_int32), ("precond", c_int32),
+        ("lane_team", c_int32),
     ]
 
 
@@ -54,7 +55,14 @@ class pppc_stats(ctypes.Structure):
         ("newton_iters", c_int64), ("pcg_iters", c_int64), ("cocg_iters", c_int64),
         ("fine_steps", c_int64), ("pppc_iters", c_int32), ("rel_res", c_double),
         ("fine_ms", c_double), ("coarse_ms", c_double), ("launches", c_int64), ("backtracks", c_int64),
+        ("pcg_lane_rounds", c_int64), ("pcg_lane_iters", c_int64), ("newton_lane_rounds", c_int64),
     ]
+
+
+class pppc_fine_plan_info(ctypes.Structure):
+    _fields_ = [("lanes_per_team", c_int32), ("teams", c_int32), ("threads_per_row", c_int32),
+                ("blocks_min", c_int32), ("blocks_max", c_int32), ("n_candidates", c_int32),
+                ("candidate_lanes", c_int32 * 16), ("candidate_ms", c_double * 16)]
 
 
 class pppc_mesh_counts(ctypes.Structure):
@@ -87,10 +95,12 @@ SIGNATURES = {
     "pppc_set_state": (c_int32, [c_void_p, c_void_p, c_int32]),
     "pppc_get_state": (c_int32, [c_void_p, c_void_p, c_int32]),
     "pppc_propagate_fine": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "pppc_propagate_fine_window": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32]),
     "pppc_coarse_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, _DPTR, c_int32]),
     "pppc_iterate": (c_int32, [c_void_p, _DPTR]),
     "pppc_solve_periodic": (c_int32, [c_void_p, c_double, c_int32, _IPTR, _DPTR]),
     "pppc_get_stats": (c_int32, [c_void_p, POINTER(pppc_stats)]),
+    "pppc_get_fine_plan": (c_int32, [c_void_p, POINTER(pppc_fine_plan_info)]),
     "pppc_set_trace": (c_int32, [c_void_p, c_int32]),
     "pppc_get_trace": (c_int32, [c_void_p, c_void_p, c_int32, _IPTR]),
     "pppc_ndof": (c_int32, [c_void_p]),

@@ -274,10 +274,13 @@ extern "C" pppc_status pppc_adjoint(pppc_handle* h, int32_t region, double tol, 
     long long c[kCounters];
     CK(cudaMemcpyAsync(c, h->counters, sizeof c, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    h->stats.newton_iters = c[0];
-    h->stats.pcg_iters = c[1];
-    h->stats.cocg_iters = c[2];
-    h->stats.backtracks = c[3];
+    h->stats.newton_iters = c[kCntNewton];
+    h->stats.pcg_iters = c[kCntPcg];
+    h->stats.cocg_iters = c[kCntCocg];
+    h->stats.backtracks = c[kCntBacktrack];
+    h->stats.pcg_lane_rounds = c[kCntPcgLaneRounds];
+    h->stats.pcg_lane_iters = c[kCntPcgLaneIters];
+    h->stats.newton_lane_rounds = c[kCntNewtonLaneRounds];
     h->stats.pppc_iters = k;
     h->stats.rel_res = rr;
     const double s = h->region_sigma[region];

@@ -8,7 +8,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pppc.h"
@@ -82,6 +85,8 @@ void free_all(pppc_handle* h) {
             cudaFree(ptr);
     }
     h->allocs.clear();
+    h->row_tables.clear();
+    h->plan = pppc_fine_plan{};
     h->has_mesh = false;
 }
 
@@ -122,7 +127,8 @@ namespace {
 
 pppc_status reset_control(pppc_handle* h) {
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
-    CK(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->st));
+    CK(cudaMemsetAsync(h->bar, 0, kMaxTeams * sizeof(GridBarrier), h->st));
+    CK(reset_team_ctl(h, h->st));
     return PPPC_OK;
 }
 
@@ -133,14 +139,196 @@ pppc_status need_ready(pppc_handle* h) {
     return PPPC_OK;
 }
 
+// ---- lane teams of the fine sweep ------------------------------------------
+//
+// The N lanes (subintervals) of a sweep are independent: they share only the
+// mesh.  A plan splits them into teams of `lanes` lanes; each team runs the
+// whole sweep on its own share of the SMs, with its own grid barrier and
+// reductions and its own [row][lanes] PCG vectors, and never waits for
+// another team.  Fewer lanes per team means fewer rows' worth of blocks per
+// barrier, a smaller SpMV gather window (lanes x 4 bytes per row) and less
+// lockstep (a team stops when its own lanes have converged); more lanes per
+// team means wider rows per thread group and more blocks per reduction.
+// Which wins depends on the mesh and N, so the choice is measured.
+
+// Fine levels each candidate marches when the plan is tuned.
+constexpr int kTuneLevels = 1;
+constexpr int kMaxCandidates = 16;
+
+// Lanes per team chosen by the tuner, by size bucket: precision, padded
+// lanes, preconditioner and floor(log2(ndof)).  Shared by every handle of
+// the process, so a bucket is timed once.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
+
+std::tuple<int, int, int, int, int> tune_key(const pppc_handle* h) {
+    int lg = 0;
+    while ((2LL << lg) <= h->hm.ndof) ++lg;
+    return {h->fp32 ? 1 : 0, h->NB, h->cfg.precond, lg, h->sms};
+}
+
+// Lanes per team that a plan may use: V 2^i (V = 4 FP32 / 2 FP64 lanes per
+// thread) dividing NB, with at most one team per SM.
+std::vector<int> team_candidates(const pppc_handle* h) {
+    const int V = h->fp32 ? 4 : 2;
+    std::vector<int> c;
+    for (int lanes = V; lanes <= h->NB && (int)c.size() < kMaxCandidates; lanes *= 2)
+        if (h->NB % lanes == 0 && h->NB / lanes <= std::min(h->sms, kMaxTeams)) c.push_back(lanes);
+    return c;
+}
+
+pppc_status row_tables_for(pppc_handle* h, int blocks, const pppc_row_tables** out) {
+    auto it = h->row_tables.find(blocks);
+    if (it == h->row_tables.end()) {
+        std::vector<int> rs, ls, lr;
+        pppc_row_tables t;
+        partition_rows(h->hm, blocks, rs, ls, lr, &t.rows_max);
+        TRY(upload(h, &t.rs, rs));
+        TRY(upload(h, &t.ls, ls));
+        TRY(upload(h, &t.lr, lr));
+        it = h->row_tables.emplace(blocks, t).first;
+    }
+    *out = &it->second;
+    return PPPC_OK;
+}
+
+// Teams of `lanes` lanes, the SMs split as evenly as the team count allows.
+pppc_status make_plan(pppc_handle* h, int lanes, pppc_fine_plan* p) {
+    pppc_fine_plan q;
+    q.lanes = lanes;
+    q.teams = h->NB / lanes;
+    q.blocks.assign(q.teams, h->sms / q.teams);
+    for (int t = 0; t < h->sms % q.teams; ++t) ++q.blocks[t];
+    const size_t budget = h->smem_optin - h->fine_static_smem - 1024;
+    for (int t = 0; t < q.teams; ++t) {
+        const pppc_row_tables* rt = nullptr;
+        TRY(row_tables_for(h, q.blocks[t], &rt));
+        int vr = 0, vw = 0;
+        choose_vec_rows(h->fp32, lanes, rt->rows_max, budget, &vr, &vw);
+        q.smem = std::max(q.smem, fine_smem(h->fp32, lanes, 1024, vr, vw ? 4 : 3));
+    }
+    *p = q;
+    return PPPC_OK;
+}
+
+// Launch the sweep `base` (one team over all lanes) as the teams of plan p:
+// per-team arguments with the team's lanes, its regions of the PCG vectors
+// and partial sums, its barrier and its row partition.
+pppc_status launch_plan(pppc_handle* h, const pppc_fine_plan& p, const FineArgs& base) {
+    const size_t ts = h->fp32 ? sizeof(float) : sizeof(double);
+    const size_t ndof = h->hm.ndof;
+    auto at = [&](void* b, size_t elems) -> void* { return b ? static_cast<char*>(b) + elems * ts : nullptr; };
+    std::vector<FineArgs> args(p.teams);
+    std::vector<int4> map(h->sms, make_int4(-1, 0, 0, 0));
+    const size_t budget = h->smem_optin - h->fine_static_smem - 1024;
+    size_t part_off = 0;
+    int first = 0;
+    for (int t = 0; t < p.teams; ++t) {
+        FineArgs a = base;
+        const int nb = p.blocks[t];
+        const pppc_row_tables& rt = h->row_tables.at(nb);
+        a.NB = p.lanes;
+        a.lane0 = t * p.lanes;
+        a.ld = h->NB;
+        a.n_teams = p.teams;
+        const size_t v = (size_t)t * ndof * p.lanes;
+        a.r = at(h->r, v);
+        a.z = at(h->z, v);
+        a.w = at(h->w, v);
+        a.p = at(h->p, v);
+        a.s = at(h->s, v);
+        a.x = at(h->x, v);
+        a.dx = at(h->dx, v);
+        a.tri_m = at(h->tri_m, v);
+        a.tri_ie = at(h->tri_ie, v);
+        a.J = at(h->J, (size_t)t * h->hm.n_slots * p.lanes);
+        a.invd_sp = at(h->invd, (size_t)t * h->hm.n_sp * p.lanes);
+        a.part = at(h->part, part_off);
+        part_off += 2 * (size_t)nb * 3 * p.lanes;   // two buffers of 3 sums per lane and block
+        a.bar = h->bar + t;
+        a.row_start = rt.rs;
+        a.long_start = rt.ls;
+        a.long_rows = rt.lr;
+        choose_vec_rows(h->fp32, p.lanes, rt.rows_max, budget, &a.vec_rows, &a.vec_w);
+        args[t] = a;
+        for (int k = 0; k < nb; ++k) map[first + k] = make_int4(t, k, nb, 0);
+        first += nb;
+    }
+    CK(cudaMemcpyAsync(h->d_team_args, args.data(), args.size() * sizeof(FineArgs), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->d_team_map, map.data(), map.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
+    CK(launch_fine_batch(h->d_team_args, h->d_team_map, h->fp32, h->sms, p.smem, h->st));
+    h->stats.launches += 1;
+    return PPPC_OK;
+}
+
+// The plan of h: fixed by cfg.lane_team, or (lane_team = 0) the bucket's
+// tuned choice, timing every candidate on the first kTuneLevels levels of
+// this sweep (from Uin, into Fout) when the bucket has none yet.
+pppc_status choose_plan(pppc_handle* h, const double* Uin, double* Fout) {
+    if (h->plan.lanes != 0) return PPPC_OK;
+    const std::vector<int> cand = team_candidates(h);
+    int lanes = -1;
+    if (h->cfg.lane_team > 0) {
+        lanes = h->cfg.lane_team;
+    } else if (h->cfg.lane_team == 0 && !cand.empty()) {
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tuned.find(tune_key(h));
+            if (it != g_tuned.end()) lanes = it->second;
+        }
+        if (lanes < 0) {
+            const size_t lane_bytes = (size_t)h->hm.ndof * h->NB * sizeof(double);
+            double best = INFINITY;
+            for (size_t c = 0; c < cand.size(); ++c) {
+                pppc_fine_plan q;
+                TRY(make_plan(h, cand[c], &q));
+                CK(cudaMemcpyAsync(Fout, Uin, lane_bytes, cudaMemcpyDeviceToDevice, h->st));
+                TRY(reset_control(h));
+                FineArgs a = fine_args(h, Fout);
+                a.n_fine = std::min(kTuneLevels, h->cfg.n_fine);
+                CK(cudaEventRecord(h->ev[0], h->st));
+                TRY(launch_plan(h, q, a));
+                CK(cudaEventRecord(h->ev[1], h->st));
+                TRY(device_status(h, "fine-sweep tuning"));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+                h->tune_ms[c] = ms;
+                if (ms < best) {
+                    best = ms;
+                    lanes = cand[c];
+                }
+            }
+            // the tuning windows are not part of the call's work
+            CK(cudaMemsetAsync(h->counters, 0, kCounters * sizeof(long long), h->st));
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tuned[tune_key(h)] = lanes;
+        }
+    }
+    if (lanes > 0) {
+        TRY(make_plan(h, lanes, &h->plan));
+    } else {
+        h->plan = pppc_fine_plan{};
+        h->plan.lanes = -1;   // one team over all lanes, the grid-wide kernel
+        h->plan.teams = 1;
+    }
+    return PPPC_OK;
+}
+
 // ---- stages of one iteration ----------------------------------------------
 
-// F = fine sweep of the lanes in Uin (F may not alias Uin).
-pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
+// F = fine sweep of the lanes in Uin (F may not alias Uin): all n_fine
+// levels, or the window of `count` levels from level `first`.
+pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout, int first = 0, int count = -1) {
     const size_t lane_bytes = (size_t)h->hm.ndof * h->NB * sizeof(double);
+    TRY(choose_plan(h, Uin, Fout));
     CK(cudaMemcpyAsync(Fout, Uin, lane_bytes, cudaMemcpyDeviceToDevice, h->st));
     TRY(reset_control(h));
     FineArgs a = fine_args(h, Fout);
+    if (count >= 0) {
+        a.level0 = first;
+        a.n_fine = count;
+    }
+    const bool one_team = h->plan.lanes < 0 || h->trace_cap > 0;   // the trace records one team's lanes
     if (h->trace_cap > 0) {
         CK(cudaMemsetAsync(h->trace_len, 0, sizeof(int), h->st));
         a.trace = h->trace;
@@ -148,8 +336,12 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
         a.trace_len = h->trace_len;
     }
     CK(cudaEventRecord(h->ev[0], h->st));
-    CK(launch_fine_sweep(a, h->fp32, h->fine_cfg, h->st));
-    h->stats.launches += 1;
+    if (one_team) {
+        CK(launch_fine_sweep(a, h->fp32, h->fine_cfg, h->st));
+        h->stats.launches += 1;
+    } else {
+        TRY(launch_plan(h, h->plan, a));
+    }
     CK(cudaEventRecord(h->ev[1], h->st));
     TRY(device_status(h, "fine propagators"));
     float ms = 0.f;
@@ -160,13 +352,24 @@ pppc_status run_fine(pppc_handle* h, const double* Uin, double* Fout) {
 
 }  // namespace
 
+cudaError_t pppc::detail::reset_team_ctl(pppc_handle* h, cudaStream_t st) {
+    return cudaMemsetAsync(h->team_ctl, 0, 4 * sizeof(long long), st);
+}
+
 FineArgs pppc::detail::fine_args(pppc_handle* h, double* Fout) {
     FineArgs a{};
     a.mesh = h->md;
     a.src = h->src;
     a.N = h->N;
     a.NB = h->NB;
+    a.ld = h->NB;
+    a.lane0 = 0;
+    a.n_teams = 1;
+    a.sweep_max = h->team_ctl;
+    a.teams_done = reinterpret_cast<unsigned int*>(h->team_ctl + 2);
     a.n_fine = h->cfg.n_fine;
+    a.level0 = 0;
+    a.n_total = h->cfg.n_fine;
     a.dt = h->dt;
     a.inv_dt = 1.0 / h->dt;
     // inexact PP-PC: looser Newton while the jumps are large (pppc_config.newton_schedule)
@@ -435,10 +638,13 @@ pppc_status end_call(pppc_handle* h) {
     long long c[kCounters];
     CK(cudaMemcpyAsync(c, h->counters, sizeof c, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
-    h->stats.newton_iters = c[0];
-    h->stats.pcg_iters = c[1];
-    h->stats.cocg_iters = c[2];
-    h->stats.backtracks = c[3];
+    h->stats.newton_iters = c[kCntNewton];
+    h->stats.pcg_iters = c[kCntPcg];
+    h->stats.cocg_iters = c[kCntCocg];
+    h->stats.backtracks = c[kCntBacktrack];
+    h->stats.pcg_lane_rounds = c[kCntPcgLaneRounds];
+    h->stats.pcg_lane_iters = c[kCntPcgLaneIters];
+    h->stats.newton_lane_rounds = c[kCntNewtonLaneRounds];
     return PPPC_OK;
 }
 
@@ -535,6 +741,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (c.precond != 0 && c.precond != 1) why = "precond must be 0 or 1";
     else if (c.predictor < 0 || c.predictor > 2) why = "predictor must be 0, 1 or 2";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
+    else if (c.lane_team < -1) why = "lane_team must be -1, 0 or a lane count";
     else if ((c.alloc == nullptr) != (c.free_fn == nullptr)) why = "alloc and free_fn must be given together";
     if (!why.empty()) {
         g_create_error = why;
@@ -805,6 +1012,18 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         choose_vec_rows(h->fp32, h->NB, rows_max, (size_t)smem_optin - 1024, &h->vec_rows, &h->vec_w);
         CK(fine_config(h->fp32, h->NB, h->vec_rows, h->vec_w ? 4 : 3, &h->fine_cfg));
         if (h->fine_cfg.blocks != nb) return fail(h, PPPC_ERR_CUDA, "fine sweep: one block per SM expected");
+        // lane teams (the plan is chosen at the first sweep)
+        h->sms = nb;
+        h->smem_optin = (size_t)smem_optin;
+        CK(fine_batch_prepare(h->fp32, &h->fine_static_smem));
+        h->plan = pppc_fine_plan{};
+        std::fill(std::begin(h->tune_ms), std::end(h->tune_ms), 0.0);
+        if (h->cfg.lane_team > 0) {
+            const std::vector<int> cand = team_candidates(h);
+            if (std::find(cand.begin(), cand.end(), h->cfg.lane_team) == cand.end())
+                return fail(h, PPPC_ERR_INVALID_ARG,
+                            "lane_team must be a lane-vector width times a power of two dividing the padded N");
+        }
     }
     CK(cocg_config(h->coarse_fp32, h->H, &h->cocg_cfg));
     // partial sums: two buffers per reduction (fine: T, COCG: FP64) and the jumps' 2 per block
@@ -812,7 +1031,11 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
     np = std::max(np, (size_t)2 * 512);
     TRY(alloc_n(h, &h->part, np));
     TRY(alloc_n(h, &h->jsums, 2));
-    TRY(alloc_n(h, &h->bar, 1));
+    TRY(alloc_n(h, &h->bar, kMaxTeams));
+    CK(cudaMemsetAsync(h->bar, 0, kMaxTeams * sizeof(GridBarrier), h->st));
+    TRY(alloc_n(h, &h->team_ctl, 4));
+    TRY(alloc_n(h, &h->d_team_args, kMaxTeams));
+    TRY(alloc_n(h, &h->d_team_map, (size_t)h->fine_cfg.blocks));
     TRY(alloc_n(h, &h->counters, kCounters));
     TRY(alloc_n(h, &h->ext, (size_t)h->N * hm.n_nodes));
     CK(cudaMemsetAsync(h->U, 0, LV * sizeof(double), h->st));
@@ -880,6 +1103,20 @@ pppc_status pppc_propagate_fine(pppc_handle* h, const double* U, double* F, int3
     TRY(run_fine(h, h->Unext, h->F));
     TRY(end_call(h));
     h->stats.fine_steps = h->cfg.n_fine;
+    return stage_out(h, h->F, F, on_device);
+}
+
+pppc_status pppc_propagate_fine_window(pppc_handle* h, const double* U, double* F, int32_t first, int32_t count,
+                                       int32_t on_device) {
+    TRY(need_ready(h));
+    if (!U || !F) return fail(h, PPPC_ERR_INVALID_ARG, "U or F is NULL");
+    if (first < 0 || count < 1 || (int64_t)first + count > h->cfg.n_fine)
+        return fail(h, PPPC_ERR_INVALID_ARG, "window [first, first + count) must lie in [0, n_fine]");
+    TRY(begin_call(h));
+    TRY(stage_in(h, U, on_device, h->Unext));
+    TRY(run_fine(h, h->Unext, h->F, first, count));
+    TRY(end_call(h));
+    h->stats.fine_steps = count;
     return stage_out(h, h->F, F, on_device);
 }
 
@@ -978,6 +1215,30 @@ pppc_status pppc_get_mesh_counts(pppc_handle* h, pppc_mesh_counts* out) {
 pppc_status pppc_get_stats(pppc_handle* h, pppc_stats* out) {
     if (!h || !out) return PPPC_ERR_INVALID_ARG;
     *out = h->stats;
+    return PPPC_OK;
+}
+
+pppc_status pppc_get_fine_plan(pppc_handle* h, pppc_fine_plan_info* out) {
+    if (!h || !out) return PPPC_ERR_INVALID_ARG;
+    if (!h->has_mesh) return fail(h, PPPC_ERR_STATE, "pppc_set_mesh has not been called");
+    std::memset(out, 0, sizeof *out);
+    const pppc_fine_plan& p = h->plan;
+    const int V = h->fp32 ? 4 : 2;
+    out->lanes_per_team = p.lanes;
+    out->teams = p.teams;
+    out->threads_per_row = p.lanes > 0 ? p.lanes / V : h->NB / V;
+    if (p.lanes > 0) {
+        out->blocks_min = *std::min_element(p.blocks.begin(), p.blocks.end());
+        out->blocks_max = *std::max_element(p.blocks.begin(), p.blocks.end());
+    } else if (p.lanes < 0) {
+        out->blocks_min = out->blocks_max = h->fine_cfg.blocks;
+    }
+    const std::vector<int> cand = team_candidates(h);
+    out->n_candidates = (int)cand.size();
+    for (size_t c = 0; c < cand.size() && c < 16; ++c) {
+        out->candidate_lanes[c] = cand[c];
+        out->candidate_ms[c] = h->tune_ms[c];
+    }
     return PPPC_OK;
 }
 

@@ -68,10 +68,21 @@ struct SourceDev {
 // c1 = area*nu, c2 = 2*area*dnu/d(B^2), s_a = grad N_a . grad A  (a = 0,1,2)
 constexpr int kElemPlanes = 5;
 
+// Arguments of the fine sweep of one lane team: the NB lanes lane0 ..
+// lane0 + NB - 1 of a problem with N lanes.  The FP64 state vectors (u,
+// uprev, uprev2, traj*, lam_out) and the element planes are shared by all
+// teams, [row][ld] with ld the problem's padded lane count, and are passed
+// un-offset (the kernel adds lane0).  The PCG vectors (r, z, w, p, s, x, dx,
+// J, invd_sp, tri_m, tri_ie) and the partial sums are the team's own,
+// [row][NB], already offset to the team's region.
 struct FineArgs {
     MeshDev mesh;
     SourceDev src;
-    int N, NB, n_fine;
+    int N, NB, n_fine;       // N: the problem's lanes; NB: this team's lanes;
+                             // n_fine: implicit-Euler steps this launch marches per lane
+    int ld, lane0;           // row stride of the state vectors; first lane of the team
+    int level0, n_total;     // first level of that window and levels per subinterval
+                             // (lane l's step s ends at t = (l n_total + level0 + s + 1) dt)
     double dt, inv_dt;
     double tol_abs;          // Newton stop on ||R||_2 per lane
     double tol_lin;          // smallest PCG forcing term
@@ -95,7 +106,10 @@ struct FineArgs {
     int vec_w;               // 1: w as well
     GridBarrier* bar;
     int* status;
-    long long* counters;     // [0] newton tests, [1] pcg iterations, [3] rounds with a backtracking lane
+    long long* counters;     // [kCounters], see kCounter* below (shared by the teams of a sweep)
+    long long* sweep_max;    // [2] per launch, zeroed before it: max over teams of Newton / PCG rounds
+    unsigned int* teams_done;// per launch, zeroed before it: teams that finished
+    int n_teams;             // teams in this launch (the last one adds sweep_max into counters)
     double* trace;           // optional [trace_cap * kTraceFields] Newton records, or null
     int trace_cap;
     int* trace_len;          // records written (may exceed trace_cap; extra ones dropped)
@@ -113,6 +127,17 @@ struct FineArgs {
     void* tri_m;             // [ndof*NB] of T: LDL^T multipliers of the chunk factorisation
     void* tri_ie;            // [ndof*NB] of T: inverse pivots
 };
+
+// Device counters of a handle, accumulated over the sweeps of one call.
+constexpr int kCounters = 8;
+constexpr int kCntNewton = 0;        // Newton rounds (lockstep per team), max over teams, summed over sweeps
+constexpr int kCntPcg = 1;           // PCG rounds, same
+constexpr int kCntCocg = 2;          // COCG iterations (lockstep over the harmonics)
+constexpr int kCntBacktrack = 3;     // Newton rounds in which some lane backtracked, summed over teams
+constexpr int kCntPcgLaneRounds = 4; // sum over teams of PCG rounds x team lanes (lane-vectors streamed)
+constexpr int kCntPcgLaneIters = 5;  // sum over lanes of the PCG iterations that lane needed
+constexpr int kCntNewtonLaneRounds = 6;  // sum over teams of Newton rounds x team lanes
+constexpr int kMaxTeams = 256;       // lane teams of one sweep (at most one block each)
 
 // One record per Newton test of the fine sweep:
 // step, Newton iteration, max over lanes of ||R||_2, lanes still iterating,

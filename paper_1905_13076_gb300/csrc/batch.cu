@@ -48,7 +48,8 @@ struct CtlSrc {
 };
 struct CtlOut {
     double js0, js1;
-    long long status, newton, pcg, cocg, backtracks;
+    long long status;
+    long long c[kCounters];   // the member's counters (kCnt*)
     long long t[4];
 };
 
@@ -60,10 +61,7 @@ __global__ void gather_ctl_kernel(const CtlSrc* src, int count, CtlOut* out) {
     o.js0 = s.jsums[0];
     o.js1 = s.jsums[1];
     o.status = *s.status;
-    o.newton = s.counters[0];
-    o.pcg = s.counters[1];
-    o.cocg = s.counters[2];
-    o.backtracks = s.counters[3];
+    for (int q = 0; q < kCounters; ++q) o.c[q] = s.counters[q];
     for (int q = 0; q < 4; ++q) o.t[q] = s.team_ns[q];
     out[c] = o;
 }
@@ -284,6 +282,7 @@ pppc_status rebuild(pppc_batch* b) {
                             b->st));
         CAP(cudaMemsetAsync(h->status, 0, sizeof(int), b->st));
         CAP(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), b->st));
+        CAP(reset_team_ctl(h, b->st));
     }
     CAP(launch_fine_batch(b->d_fargs, b->d_fmap, b->fp32, b->sms, b->fine_smem_launch, b->st));
     b->fine_kernels += 1;
@@ -355,10 +354,14 @@ pppc_status check_members(pppc_batch* b, const char* where) {
 void update_member_stats(pppc_batch* b) {
     for (int c = 0; c < b->count; ++c) {
         pppc_stats& s = b->m[c]->stats;
-        s.newton_iters = b->h_ctl[c].newton;
-        s.pcg_iters = b->h_ctl[c].pcg;
-        s.cocg_iters = b->h_ctl[c].cocg;
-        s.backtracks = b->h_ctl[c].backtracks;
+        const long long* k = b->h_ctl[c].c;
+        s.newton_iters = k[kCntNewton];
+        s.pcg_iters = k[kCntPcg];
+        s.cocg_iters = k[kCntCocg];
+        s.backtracks = k[kCntBacktrack];
+        s.pcg_lane_rounds = k[kCntPcgLaneRounds];
+        s.pcg_lane_iters = k[kCntPcgLaneIters];
+        s.newton_lane_rounds = k[kCntNewtonLaneRounds];
     }
 }
 

@@ -72,12 +72,29 @@ __global__ void jumps_kernel(int ndof, int N, int NB, const double* U, const dou
     }
 }
 
-__global__ void sum_pairs_kernel(int nblocks, const double* part, double* sums) {
-    if (threadIdx.x < 2) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += part[2 * b + threadIdx.x];
-        sums[threadIdx.x] = s;
+// sums[v] = sum over the nblocks partial pairs part[2 b + v], v = 0, 1: each
+// of 256 threads adds a strided share of the partials, then a fixed-order
+// tree in shared memory (deterministic, like every reduction here).
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) sum_pairs_kernel(int nblocks, const double* part, double* sums) {
+    __shared__ double red[2][kSumThreads];
+    const int t = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int q = t; q < nblocks; q += kSumThreads) {
+        a += part[2 * q];
+        b += part[2 * q + 1];
     }
+    red[0][t] = a;
+    red[1][t] = b;
+    __syncthreads();
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            red[0][t] += red[0][t + w];
+            red[1][t] += red[1][t + w];
+        }
+        __syncthreads();
+    }
+    if (t < 2) sums[t] = red[t][0];
 }
 
 // ------------------------------------------------- coarse linearisation --
@@ -482,7 +499,7 @@ __global__ void lanes_to_state_kernel(int n_nodes, int N, int NB, const int* dof
 void launch_jumps(int ndof, int N, int NB, const double* U, const double* F, double* d, double* part,
                   double* sums, cudaStream_t st) {
     jumps_kernel<<<kJumpBlocks, 256, 0, st>>>(ndof, N, NB, U, F, d, part);
-    sum_pairs_kernel<<<1, 32, 0, st>>>(kJumpBlocks, part, sums);
+    sum_pairs_kernel<<<1, kSumThreads, 0, st>>>(kJumpBlocks, part, sums);
 }
 
 void launch_kbar(const MeshDev& m, int N, int NB, int lin, const double* elem, double* Kbar,

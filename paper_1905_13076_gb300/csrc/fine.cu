@@ -211,11 +211,11 @@ __device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0,
 template <typename T, int V>
 __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, int row0, int re, int RB, int l0,
                                            const double* s_I, double* accR, T* accz, T* xB, size_t vo) {
-    const int NB = a.NB;
-    const size_t P = (size_t)m.n_nl * NB;
-    const double* u = a.u;
-    const double* uprev = a.uprev;
-    const double* E = a.elem;
+    const int NB = a.NB, LD = a.ld;
+    const size_t P = (size_t)m.n_nl * LD;
+    const double* u = a.u + a.lane0;
+    const double* uprev = a.uprev + a.lane0;
+    const double* E = a.elem + a.lane0;
     T* r = static_cast<T*>(a.r);
     T* z = static_cast<T*>(a.z);
     T* J = static_cast<T*>(a.J);
@@ -225,9 +225,10 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
     for (int i = row0; i < re; i += RB) {
                 const int kb = m.rowptr[i], ke = m.rowptr[i + 1];
                 const int slot0 = m.row_slot[i];
-                const size_t o = (size_t)i * NB + l0;
+                const size_t o = (size_t)i * NB + l0;    // team vectors
+                const size_t os = (size_t)i * LD + l0;   // state vectors
                 // K_lin u in difference form: sum_{j != i} K_ij (u_j - u_i) + dlin_i u_i
-                const Lanes<double, V> ui = ldv<double, V>(u + o);
+                const Lanes<double, V> ui = ldv<double, V>(u + os);
                 const double dl = m.dlin[i];
                 double acc[V];
 #pragma unroll
@@ -238,7 +239,7 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                         const int j = m.col[k];
                         if (j == i) continue;
                         const double kv = m.Klin[k];
-                        const Lanes<double, V> uj = ldv<double, V>(u + (size_t)j * NB + l0);
+                        const Lanes<double, V> uj = ldv<double, V>(u + (size_t)j * LD + l0);
 #pragma unroll
                         for (int h = 0; h < V; ++h) acc[h] += kv * (uj.v[h] - ui.v[h]);
                     }
@@ -252,8 +253,8 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                         const int j = m.col[k];
                         const double kv = m.Klin[k];
                         const double mv = m.Mslot[sl] * a.inv_dt;
-                        const Lanes<double, V> uj = ldv<double, V>(u + (size_t)j * NB + l0);
-                        const Lanes<double, V> upj = ldv<double, V>(uprev + (size_t)j * NB + l0);
+                        const Lanes<double, V> uj = ldv<double, V>(u + (size_t)j * LD + l0);
+                        const Lanes<double, V> upj = ldv<double, V>(uprev + (size_t)j * LD + l0);
                         const double kl = (j == i) ? 0.0 : kv;
                         double Jv[V];
 #pragma unroll
@@ -268,7 +269,7 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                             // area * cap: c1 = area * nu above it marks a capped element
                             const double c1cap = std::is_same<T, float>::value ? kNuCapFp32 * m.nl_geom[8 * (size_t)q]
                                                                               : 0.0;
-                            const size_t eo = (size_t)q * NB + l0;
+                            const size_t eo = (size_t)q * LD + l0;
                             const Lanes<double, V> c1 = ldv<double, V>(E + eo);
                             const Lanes<double, V> c2 = ldv<double, V>(E + P + eo);
                             const Lanes<double, V> sa = ldv<double, V>(E + (2 + ia) * P + eo);
@@ -325,13 +326,13 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
 template <typename T, int V>
 __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, int row0, int re, int RB, int l0, int j,
                                           double* accR, T* accz, double* accb, T* xB, size_t vo) {
-    const int NB = a.NB, N = a.N;
-    const size_t P = (size_t)m.n_nl * NB;
-    const size_t lv = (size_t)m.ndof * NB;
-    const double* lam = a.u;
-    const double* lnext = a.uprev;
-    const double* E = a.elem;
-    const double* um = a.traj + (size_t)j * lv;
+    const int NB = a.NB, N = a.N, LD = a.ld;
+    const size_t P = (size_t)m.n_nl * LD;
+    const size_t lv = (size_t)m.ndof * LD;
+    const double* lam = a.u + a.lane0;
+    const double* lnext = a.uprev + a.lane0;
+    const double* E = a.elem + a.lane0;
+    const double* um = a.traj + a.lane0 + (size_t)j * lv;
     const double* ump = um - lv;
     const bool last = j == a.n_fine;   // du^{m+1} from the next lane's levels 0, 1
     T* r = static_cast<T*>(a.r);
@@ -343,7 +344,7 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
     for (int i = row0; i < re; i += RB) {
         const int kb = m.rowptr[i], ke = m.rowptr[i + 1];
         const int slot0 = m.row_slot[i];
-        const size_t o = (size_t)i * NB + l0;
+        const size_t o = (size_t)i * NB + l0;   // team vectors
         double acc[V], bb[V];
 #pragma unroll
         for (int h = 0; h < V; ++h) acc[h] = bb[h] = 0.0;
@@ -351,7 +352,7 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
         if (slot0 < 0) {
             for (int k = kb; k < ke; ++k) {
                 const double kv = m.Klin[k];
-                const Lanes<double, V> lj = ldv<double, V>(lam + (size_t)m.col[k] * NB + l0);
+                const Lanes<double, V> lj = ldv<double, V>(lam + (size_t)m.col[k] * LD + l0);
 #pragma unroll
                 for (int h = 0; h < V; ++h) acc[h] += kv * lj.v[h];
             }
@@ -363,7 +364,7 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
             for (int k = kb; k < ke; ++k) {
                 const int sl = slot0 + (k - kb);
                 const int jc = m.col[k];
-                const size_t oc = (size_t)jc * NB + l0;
+                const size_t oc = (size_t)jc * LD + l0;   // state vectors
                 const double kv = m.Klin[k];
                 const double ms = m.Mslot[sl];
                 const double mv = ms * a.inv_dt;
@@ -380,8 +381,8 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
                     } else {
 #pragma unroll
                         for (int h = 0; h < V; ++h) {
-                            const int ln = (l0 + h + 1) % N;
-                            const size_t on = (size_t)jc * NB + ln;
+                            const int ln = (a.lane0 + l0 + h + 1) % N;   // the next subinterval
+                            const size_t on = (size_t)jc * LD + ln;
                             dd[h] = (u0.v[h] - u1.v[h]) - (a.traj[lv + on] - a.traj[on]);
                         }
                     }
@@ -397,7 +398,7 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
                     const int q = pk / 9, ia = (pk / 3) % 3, ib = pk % 3;
                     const double ab = m.nlc_ab[c];
                     const double c1cap = std::is_same<T, float>::value ? kNuCapFp32 * m.nl_geom[8 * (size_t)q] : 0.0;
-                    const size_t eo = (size_t)q * NB + l0;
+                    const size_t eo = (size_t)q * LD + l0;
                     const Lanes<double, V> c1 = ldv<double, V>(E + eo);
                     const Lanes<double, V> c2 = ldv<double, V>(E + P + eo);
                     const Lanes<double, V> sa = ldv<double, V>(E + (2 + ia) * P + eo);
@@ -582,8 +583,8 @@ __device__ __noinline__ void tri_solve(const FineArgs& a, int rs, int re, int RB
 // Newton step (coef 1), u += coef * dx for lanes that backtrack (coef < 0),
 // nothing for the others.  Out of line for the same reason as residual_rows.
 template <typename T, int V>
-__device__ __noinline__ void apply_steps(double* u, const T* xB, size_t vo, T* dx, const double* s_coef, int row0,
-                                         int re, int RB, int l0, int NB) {
+__device__ __noinline__ void apply_steps(double* u, int LD, const T* xB, size_t vo, T* dx, const double* s_coef,
+                                         int row0, int re, int RB, int l0, int NB) {
     double cf[V];
     bool step = false, keep = false, back = false;
 #pragma unroll
@@ -596,8 +597,9 @@ __device__ __noinline__ void apply_steps(double* u, const T* xB, size_t vo, T* d
     if (!step && !back) return;
     for (int i = row0; i < re; i += RB) {
         const size_t o = (size_t)i * NB + l0;
+        const size_t os = (size_t)i * LD + l0;
         const Lanes<T, V> xi = ldv<T, V>(xB + (o - vo));
-        Lanes<double, V> ui = ldv<double, V>(u + o);
+        Lanes<double, V> ui = ldv<double, V>(u + os);
         Lanes<T, V> di;
         if (back || keep) di = ldv<T, V>(dx + o);
 #pragma unroll
@@ -609,7 +611,7 @@ __device__ __noinline__ void apply_steps(double* u, const T* xB, size_t vo, T* d
                 ui.v[h] += cf[h] * (double)di.v[h];
             }
         }
-        stv<double, V>(u + o, ui);
+        stv<double, V>(u + os, ui);
         if (step) stv<T, V>(dx + o, di);
     }
 }
@@ -622,8 +624,8 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
     constexpr int V = sizeof(T) == 4 ? 4 : 2;   // lanes per thread: one 16-byte access
     using RT = T;                               // reductions run in the PCG precision
     extern __shared__ double smem[];
-    const MeshDev m = a.mesh;
-    const int NB = a.NB, G = NB / V;
+    const MeshDev& m = a.mesh;
+    const int NB = a.NB, G = NB / V, LD = a.ld, lane0 = a.lane0;
     const int tid = threadIdx.x, g = tid % G, rb = tid / G, RB = blockDim.x / G;
     const int l0 = V * g;
     double* s_I = smem;            // current I(t) of each lane at the new time level
@@ -642,6 +644,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
     int* s_newton = reinterpret_cast<int*>(s_tmp + blockDim.x);
     int* s_pcg = s_newton + NB;
     int* s_nacc = s_pcg + NB;      // accepted Newton steps of the current time step
+    int* s_lit = s_nacc + NB;      // PCG iterations each lane needed during this launch
     __shared__ int s_err;
     RT* part_buf[2] = {static_cast<RT*>(a.part), static_cast<RT*>(a.part) + (size_t)nblk * NV * NB};
     int parity = 0;
@@ -658,10 +661,11 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                                                    : reinterpret_cast<const T*>(m.Klin);
     const T* invdiag_linT = std::is_same<T, float>::value ? reinterpret_cast<const T*>(m.invdiag_lin32)
                                                           : reinterpret_cast<const T*>(m.invdiag_lin);
-    double* u = a.u;
-    double* uprev = a.uprev;
-    const double* E = a.elem;
-    const size_t P = (size_t)m.n_nl * NB;
+    // state vectors from this team's first lane on, row stride LD
+    double* u = a.u + lane0;
+    double* uprev = a.uprev + lane0;
+    double* uprev2 = a.uprev2 ? a.uprev2 + lane0 : nullptr;
+    double* traj_out = a.traj_out ? a.traj_out + lane0 : nullptr;
     // this block owns the contiguous rows [rs, re)
     const int rs = a.row_start[bid], re = a.row_start[bid + 1];
     // p, s, x, w are only touched by their owning block: when a.vec_rows > 0
@@ -674,7 +678,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
     size_t wo = 0;
     if (a.vec_rows > 0) {
         T* sv = reinterpret_cast<T*>(
-            (reinterpret_cast<uintptr_t>(s_nacc + NB) + 15) & ~static_cast<uintptr_t>(15));
+            (reinterpret_cast<uintptr_t>(s_lit + NB) + 15) & ~static_cast<uintptr_t>(15));
         const size_t len = (size_t)a.vec_rows * NB;
         pB = sv;
         sB = sv + len;
@@ -694,18 +698,20 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
     __shared__ long long s_cnt[4];
     if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
     if (tid == 0) s_err = 0;
+    for (int l = tid; l < NB; l += blockDim.x) s_lit[l] = 0;
     if (a.team_ns && bid == 0 && tid == 0) a.team_ns[0] = global_ns();
 
     for (int step = 0; step < a.n_fine; ++step) {
         for (int l = tid; l < NB; l += blockDim.x) {
             double I = 0.0;
-            if (l < a.N) {
-                const double t = (double)((long long)l * a.n_fine + step + 1) * a.dt;
+            const int lg = lane0 + l;   // the problem's lane = subinterval lg + 1
+            if (lg < a.N) {
+                const double t = (double)((long long)lg * a.n_total + a.level0 + step + 1) * a.dt;
                 for (int h = 0; h < a.src.n_harm; ++h)
                     I += a.src.amp[h] * sin(2.0 * kPi * a.src.freq[h] * t + a.src.phase[h]);
             }
             s_I[l] = I;
-            s_newton[l] = (l < a.N);
+            s_newton[l] = (lg < a.N);
             s_nacc[l] = 0;
             s_lam[l] = 1.0;
         }
@@ -716,15 +722,15 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
         const bool extrap = !a.adjoint && a.predictor && step > 0;
         const bool quad = a.predictor == 2 && !a.adjoint;   // keeps u^{m-2} in uprev2
         for (int i = row0; i < re; i += RB) {
-            const size_t o = (size_t)i * NB + l0;
+            const size_t o = (size_t)i * LD + l0;
             const Lanes<double, V> um = ldv<double, V>(u + o);
-            if (a.traj_out && step == 0) stv<double, V>(a.traj_out + o, um);
+            if (traj_out && step == 0) stv<double, V>(traj_out + o, um);
             if (extrap || quad) {
                 const Lanes<double, V> uo = ldv<double, V>(uprev + o);
                 if (extrap) {
                     Lanes<double, V> un;
                     if (quad && step > 1) {
-                        const Lanes<double, V> uo2 = ldv<double, V>(a.uprev2 + o);
+                        const Lanes<double, V> uo2 = ldv<double, V>(uprev2 + o);
 #pragma unroll
                         for (int h = 0; h < V; ++h) un.v[h] = 3.0 * (um.v[h] - uo.v[h]) + uo2.v[h];
                     } else {
@@ -733,7 +739,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     }
                     stv<double, V>(u + o, un);
                 }
-                if (quad) stv<double, V>(a.uprev2 + o, uo);
+                if (quad) stv<double, V>(uprev2 + o, uo);
             }
             stv<double, V>(uprev + o, um);
         }
@@ -741,9 +747,9 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
         {
             // element data of the state the Jacobian is taken at: the Newton
             // iterate, or in the adjoint the forward state u^m (fixed for the level)
-            const double* eu = a.adjoint ? a.traj + (size_t)j * m.ndof * NB : u;
+            const double* eu = a.adjoint ? a.traj + (size_t)j * m.ndof * LD : a.u;
             for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
-                elem_compute(m, NB, eu, a.elem, (int)(it / NB), (int)(it % NB));
+                elem_compute(m, LD, eu, a.elem, (int)(it / NB), lane0 + (int)(it % NB));
         }
         if (!grid_sync(a.bar, a.status, bid, nblk)) return;
 
@@ -997,6 +1003,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                                 s_gold[l] = (double)gg;
                                 s_aold[l] = al;
                                 on = 1;
+                                if (bid == 0) ++s_lit[l];
                             }
                         }
                     }
@@ -1032,8 +1039,9 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     Lanes<T, V> pn, sn, rn, xn;
 #pragma unroll
                     for (int h = 0; h < V; ++h) {
-                        pn.v[h] = zi.v[h] + bev[h] * pi.v[h];
-                        sn.v[h] = wi.v[h] + bev[h] * si.v[h];
+                        // first iteration: p = z, s = w (whatever p and s held before)
+                        pn.v[h] = k == 0 ? zi.v[h] : zi.v[h] + bev[h] * pi.v[h];
+                        sn.v[h] = k == 0 ? wi.v[h] : wi.v[h] + bev[h] * si.v[h];
                         rn.v[h] = ri.v[h] - alv[h] * sn.v[h];
                         xn.v[h] = xi.v[h] + alv[h] * pn.v[h];
                     }
@@ -1064,27 +1072,42 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                 if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             }
             // ---- own rows: apply this round's steps, then element data at the new u
-            apply_steps<T, V>(u, xB, vo, static_cast<T*>(a.dx), s_eta + NB, row0, re, RB, l0, NB);
+            apply_steps<T, V>(u, LD, xB, vo, static_cast<T*>(a.dx), s_eta + NB, row0, re, RB, l0, NB);
             if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             if (!a.adjoint) {
                 for (long long it = bid * (long long)blockDim.x + tid; it < n_elem_items; it += gthreads)
-                    elem_compute(m, NB, u, a.elem, (int)(it / NB), (int)(it % NB));
+                    elem_compute(m, LD, a.u, a.elem, (int)(it / NB), lane0 + (int)(it % NB));
                 if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             }
         }
         // ---- record the level just solved (own rows)
-        double* rec = a.adjoint ? (a.lam_out ? a.lam_out + (size_t)(j - 1) * m.ndof * NB : nullptr)
-                                : (a.traj_out ? a.traj_out + (size_t)(step + 1) * m.ndof * NB : nullptr);
+        double* rec = a.adjoint ? (a.lam_out ? a.lam_out + lane0 + (size_t)(j - 1) * m.ndof * LD : nullptr)
+                                : (traj_out ? traj_out + (size_t)(step + 1) * m.ndof * LD : nullptr);
         if (rec)
             for (int i = row0; i < re; i += RB) {
-                const size_t o = (size_t)i * NB + l0;
+                const size_t o = (size_t)i * LD + l0;
                 stv<double, V>(rec + o, ldv<double, V>(u + o));
             }
     }
     if (bid == 0 && tid == 0) {
-        a.counters[0] += s_cnt[0];
-        a.counters[1] += s_cnt[1];
-        a.counters[3] += s_cnt[3];
+        // per team: rounds are this team's lockstep rounds; the last team to
+        // finish adds the maxima over teams (the launch's critical path)
+        long long useful = 0;
+        for (int l = 0; l < NB; ++l) useful += s_lit[l];
+        atomicMax(&a.sweep_max[0], s_cnt[0]);
+        atomicMax(&a.sweep_max[1], s_cnt[1]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.counters[kCntBacktrack]), (unsigned long long)s_cnt[3]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.counters[kCntPcgLaneRounds]),
+                  (unsigned long long)(s_cnt[1] * NB));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.counters[kCntPcgLaneIters]), (unsigned long long)useful);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&a.counters[kCntNewtonLaneRounds]),
+                  (unsigned long long)(s_cnt[0] * NB));
+        __threadfence();
+        if (atomicAdd(a.teams_done, 1u) == (unsigned int)a.n_teams - 1u) {
+            __threadfence();
+            a.counters[kCntNewton] += atomicAdd(reinterpret_cast<unsigned long long*>(&a.sweep_max[0]), 0ull);
+            a.counters[kCntPcg] += atomicAdd(reinterpret_cast<unsigned long long*>(&a.sweep_max[1]), 0ull);
+        }
         if (a.team_ns) a.team_ns[1] = global_ns();
     }
 }
@@ -1118,7 +1141,7 @@ size_t fine_smem(bool fp32, int NB, int threads, int vec_rows, int vec_count) {
     const int slots = red_slots(NB / V, threads);
     const size_t rt = fp32 ? sizeof(float) : sizeof(double);
     size_t b = (size_t)10 * NB * sizeof(double) + (size_t)(NV * slots * NB + NV * NB + threads) * rt +
-               3 * NB * sizeof(int);
+               4 * NB * sizeof(int);
     if (vec_rows > 0) b += 16 + (size_t)vec_count * vec_rows * NB * rt;
     return b;
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -10,6 +11,24 @@
 #include "args.h"
 #include "kernels.h"
 #include "mesh_host.h"
+
+// Row partition of the fine sweep for one team size (blocks), on the device.
+struct pppc_row_tables {
+    int* rs = nullptr;     // [blocks + 1] first row of each block
+    int* ls = nullptr;     // [blocks + 1] ranges of lr per block
+    int* lr = nullptr;     // long rows by owning block
+    int rows_max = 0;
+};
+
+// How the fine sweep of one handle is split into lane teams: `teams` teams of
+// `lanes` lanes each, team t on blocks[t] blocks; the per-team kernel
+// arguments (rebuilt per sweep) and the block -> (team, block in team, team
+// size) map live on the device.
+struct pppc_fine_plan {
+    int lanes = 0, teams = 0;
+    std::vector<int> blocks;
+    size_t smem = 0;
+};
 
 struct pppc_handle {
     using HostMesh = pppc::HostMesh;
@@ -44,9 +63,18 @@ struct pppc_handle {
     void *cx = nullptr, *cr = nullptr, *cz = nullptr, *cw = nullptr, *cp = nullptr, *cs = nullptr, *cinvd = nullptr;
     // reductions and control
     double *part = nullptr, *jsums = nullptr, *scalars = nullptr;
-    GridBarrier* bar = nullptr;
+    GridBarrier* bar = nullptr;     // [kMaxTeams]: one per lane team (bar[0] for every other launch)
     int* status = nullptr;
     long long* counters = nullptr;
+    long long* team_ctl = nullptr;  // [4]: max over teams of Newton / PCG rounds, teams done (per sweep)
+    // lane teams of the fine sweep
+    pppc_fine_plan plan;            // the plan in use (lanes == 0: not chosen yet)
+    std::map<int, pppc_row_tables> row_tables;   // by team size
+    pppc::FineArgs* d_team_args = nullptr;   // [kMaxTeams]
+    int4* d_team_map = nullptr;        // [SMs]
+    int sms = 0;
+    size_t fine_static_smem = 0, smem_optin = 0;
+    double tune_ms[16] = {0};          // tuner: time of each candidate (lanes = V * 2^i), 0 if not timed
     double* ext = nullptr;   // [N][n_nodes] staging for host states
     double* trace = nullptr; // Newton trace of the fine sweep (optional)
     int* trace_len = nullptr;
@@ -76,17 +104,15 @@ struct pppc_handle {
 namespace pppc {
 namespace detail {
 
-// Device counters of a handle: newton tests, pcg iterations, cocg
-// iterations, fine-sweep rounds in which some lane backtracked.
-constexpr int kCounters = 4;
-
 // Record msg as h's last error and return s.
 pppc_status fail(pppc_handle* h, pppc_status s, const std::string& msg);
 // Synchronise h's stream and map h's device status word to a pppc_status.
 pppc_status device_status(pppc_handle* h, const char* where);
-// Arguments of h's fine sweep writing F into Fout, with h's own row
-// partition (callers may replace the partition fields).
+// Arguments of h's fine sweep writing F into Fout, as one team over all
+// lanes with h's own row partition (callers may replace the partition fields).
 FineArgs fine_args(pppc_handle* h, double* Fout);
+// Zero h's per-sweep team control words (sweep maxima, teams done) on stream st.
+cudaError_t reset_team_ctl(pppc_handle* h, cudaStream_t st);
 // Arguments of h's batched harmonic solve (Eq. 13).
 CocgArgs cocg_args(pppc_handle* h);
 // Stages of one iteration on h's stream: mesh and source present; control

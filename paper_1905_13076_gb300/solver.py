@@ -43,7 +43,8 @@ class PPPC:
                  coarse_lin: str = "avg_jacobian", tol_newton: float = 1e-10, max_newton: int = 30,
                  tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
                  max_coarse: int = 20000, eta0: float = 1e-2, predictor: int = 1, method: str = "pppc",
-                 coarse_at: str = "U", newton_schedule: bool = False, precond: str = "jacobi", stream=None):
+                 coarse_at: str = "U", newton_schedule: bool = False, precond: str = "jacobi",
+                 lane_team: int = 0, stream=None):
         self._lib = _lib.load()
         cfg = pppc_config()
         self._lib.pppc_config_default(ctypes.byref(cfg))
@@ -58,6 +59,7 @@ class PPPC:
         cfg.coarse_at = _lib.COARSE_AT[coarse_at]
         cfg.newton_schedule = int(bool(newton_schedule))
         cfg.precond = {"jacobi": 0, "tridiag": 1}[precond]
+        cfg.lane_team = int(lane_team)
         cfg.stream = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
         self.cfg = cfg
         h = ctypes.c_void_p()
@@ -165,6 +167,14 @@ class PPPC:
         self._check(self._lib.pppc_propagate_fine(self._h, ptr, optr, dev))
         return out
 
+    def propagate_fine_window(self, U, first: int, count: int):
+        """Levels first..first+count of every subinterval: U[j] at T_j + first dt
+        -> F[j] at T_j + (first + count) dt (Eq. 3 on part of each subinterval)."""
+        keep, ptr, dev = self._ptr_in(U)
+        out, optr = self._out_like(U)
+        self._check(self._lib.pppc_propagate_fine_window(self._h, ptr, optr, int(first), int(count), dev))
+        return out
+
     def coarse_update(self, U, F):
         """U^{k+1} from U^k and F^k (Eq. 4 through Eqs. 9-14); returns (U_new, rel_res)."""
         ku, pu, dev = self._ptr_in(U)
@@ -207,6 +217,15 @@ class PPPC:
         c = _lib.pppc_mesh_counts()
         self._check(self._lib.pppc_get_mesh_counts(self._h, ctypes.byref(c)))
         return {k: getattr(c, k) for k, _ in _lib.pppc_mesh_counts._fields_}
+
+    def fine_plan(self) -> dict:
+        """Lane-team split of the fine sweep in use and the tuner's timings."""
+        p = _lib.pppc_fine_plan_info()
+        self._check(self._lib.pppc_get_fine_plan(self._h, ctypes.byref(p)))
+        n = p.n_candidates
+        return {"lanes_per_team": p.lanes_per_team, "teams": p.teams, "threads_per_row": p.threads_per_row,
+                "blocks_min": p.blocks_min, "blocks_max": p.blocks_max,
+                "candidates": list(p.candidate_lanes[:n]), "candidate_ms": list(p.candidate_ms[:n])}
 
     def stats(self) -> dict:
         s = pppc_stats()

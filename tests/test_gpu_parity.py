@@ -388,3 +388,86 @@ def test_kernels_report_sm103(library):
     v = ctypes.c_int32(0)
     assert library.pppc_binary_version(ctypes.byref(v)) == 0
     assert v.value == 103
+
+
+def test_fine_window_matches_oracle_steps():
+    """A window of the fine sweep: every subinterval j+1 marches levels
+    first..first+count from the given state.  The oracle takes the same
+    implicit-Euler steps (Eq. 3) at the same global time levels; chained
+    windows reproduce the whole sweep."""
+    from oracle.stepping import ie_step
+
+    prob = workload("small")
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    first, count = 7, 5
+    dt = prob.T / (prob.N * prob.n_fine)
+    ref = np.empty((prob.N, m.ndof))
+    for j in range(prob.N):
+        u = U0[j, m.free].copy()
+        for q in range(count):
+            s = j * prob.n_fine + first + q + 1
+            u, _ = ie_step(m, u, s * dt, dt)
+        ref[j] = u
+    with gpu_solver(prob, tol_lin=1e-12) as s:
+        Fw = s.propagate_fine_window(U0, first, count)
+        assert s.stats()["fine_steps"] == count
+        assert rel(free(prob, Fw), ref) < TOL64
+        full = s.propagate_fine(U0)
+        a = s.propagate_fine_window(U0, 0, first)
+        b = s.propagate_fine_window(a, first, prob.n_fine - first)
+        assert rel(free(prob, b), free(prob, full)) < TOL64
+        for bad in [(-1, 2), (0, 0), (prob.n_fine - 1, 2)]:
+            with pytest.raises(Exception):
+                s.propagate_fine_window(U0, *bad)
+
+
+@pytest.mark.parametrize("precision,tol,lanes", [("fp64", TOL64, -1), ("fp64", TOL64, 2), ("fp64", TOL64, 4),
+                                                 ("fp64", TOL64, 16), ("mixed", TOL_MIXED, 4),
+                                                 ("mixed", TOL_MIXED, 8), ("mixed", TOL_MIXED, 16)])
+def test_lane_teams_match_oracle(precision, tol, lanes):
+    """The fine sweep split into lane teams (every team of `lanes` lanes runs
+    on its own share of the SMs) computes the same propagators (Eqs. 2-3) for
+    every split; -1 is one team over all lanes."""
+    prob = workload("small")
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    ref = fine_sweep(m, free(prob, U0), prob.N, prob.n_fine, prob.T)
+    with gpu_solver(prob, precision=precision, lane_team=lanes, tol_lin=1e-12 if precision == "fp64" else 1e-6,
+                    tol_newton=1e-10) as s:
+        F = s.propagate_fine(U0)
+        plan = s.fine_plan()
+        st = s.stats()
+    assert rel(free(prob, F), ref) < tol
+    assert plan["lanes_per_team"] == lanes
+    if lanes > 0:
+        assert plan["teams"] == 16 // lanes
+        assert plan["blocks_min"] >= 1 and plan["blocks_max"] - plan["blocks_min"] <= 1
+    # lanes needed <= lane-vectors streamed; the critical path is one team's rounds
+    assert 0 < st["pcg_lane_iters"] <= st["pcg_lane_rounds"]
+    assert st["pcg_iters"] * (lanes if lanes > 0 else 16) <= st["pcg_lane_rounds"]
+    if lanes < 0:
+        assert st["pcg_lane_rounds"] == 16 * st["pcg_iters"]
+
+
+def test_lane_team_tuner_times_every_candidate():
+    """With lane_team = 0 the first sweep of a new size bucket times every
+    candidate split on one fine level and keeps the fastest; the sweep's
+    result does not depend on it."""
+    prob = workload("small", N=8, n_fine=6)
+    m = FEModel(prob)
+    U0 = physical_states(prob)
+    ref = fine_sweep(m, free(prob, U0), prob.N, prob.n_fine, prob.T)
+    with gpu_solver(prob, precision="fp64", tol_lin=1e-12) as s:
+        assert s.fine_plan()["lanes_per_team"] == 0          # not chosen before the first sweep
+        F = s.propagate_fine(U0)
+        plan = s.fine_plan()
+    assert plan["candidates"] == [2, 4, 8]
+    assert all(t > 0 for t in plan["candidate_ms"])
+    best = plan["candidates"][int(np.argmin(plan["candidate_ms"]))]
+    assert plan["lanes_per_team"] == best
+    assert rel(free(prob, F), ref) < TOL64
+    with gpu_solver(prob, precision="fp64") as s2:                # same bucket: the choice is reused
+        s2.propagate_fine(U0)
+        p2 = s2.fine_plan()
+    assert p2["lanes_per_team"] == best and all(t == 0 for t in p2["candidate_ms"])
