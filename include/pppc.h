@@ -132,7 +132,15 @@ typedef struct pppc_config {
                                 the last ones at tol_newton (default 0: always tol_newton) */
     int32_t precond;      /* fine PCG preconditioner: 0 Jacobi (default); 1 the tridiagonal part of
                              every 4 consecutive rows, factorised per lane (row order should follow
-                             the mesh's strongest couplings, e.g. the rings of a polar mesh) */
+                             the mesh's strongest couplings, e.g. the rings of a polar mesh);
+                             2 one V-cycle of smoothed-aggregation algebraic multigrid: the
+                             aggregates and prolongators are built once by pppc_set_mesh from
+                             the Newton matrix at zero field, each subinterval's coarse matrices
+                             are the Galerkin products of its own Jacobian (rebuilt every Newton
+                             iteration), with l1-Jacobi smoothing on every level, so the
+                             preconditioner stays symmetric positive definite for every lane
+                             and its iteration count hardly grows with the mesh; a mesh too
+                             small to coarsen falls back to Jacobi */
     int32_t lane_team;    /* how the N subintervals of a fine sweep share the GPU.  The sweep's
                              lanes are independent, so they run as teams of lane_team lanes, each
                              team on its own share of the SMs with its own barriers and
@@ -308,6 +316,8 @@ typedef struct pppc_fine_plan_info {
     int32_t candidate_lanes[16];
     double candidate_ms[16];    /* device time of one fine level per candidate, 0 if not timed
                                    by this handle (its bucket had been tuned before) */
+    int32_t amg_levels;         /* multigrid levels of precond = 2 (0: not in use) */
+    int32_t amg_rows[10];       /* rows of each level, finest first */
 } pppc_fine_plan_info;
 pppc_status pppc_get_fine_plan(pppc_handle* h, pppc_fine_plan_info* out);
 

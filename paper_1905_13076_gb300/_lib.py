@@ -62,7 +62,8 @@ class pppc_stats(ctypes.Structure):
 class pppc_fine_plan_info(ctypes.Structure):
     _fields_ = [("lanes_per_team", c_int32), ("teams", c_int32), ("threads_per_row", c_int32),
                 ("blocks_min", c_int32), ("blocks_max", c_int32), ("n_candidates", c_int32),
-                ("candidate_lanes", c_int32 * 16), ("candidate_ms", c_double * 16)]
+                ("candidate_lanes", c_int32 * 16), ("candidate_ms", c_double * 16), ("amg_levels", c_int32),
+                ("amg_rows", c_int32 * 10)]
 
 
 class pppc_mesh_counts(ctypes.Structure):

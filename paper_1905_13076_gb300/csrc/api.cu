@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/pppc.h"
+#include "amg_host.h"
 #include "args.h"
 #include "handle.h"
 #include "kernels.h"
@@ -36,6 +37,8 @@ constexpr double kNewtonLoose = 1e-6;
 // = 1); the kernel's chunk solve is specialised for it (kTri in fine.cu).
 constexpr int kTriChunk = 4;
 constexpr double kNewtonFactor = 1e-3;
+// l1-Jacobi sweeps on the coarsest multigrid level
+constexpr int kAmgCoarsestSweeps = 2;
 }
 
 
@@ -245,6 +248,7 @@ pppc_status launch_plan(pppc_handle* h, const pppc_fine_plan& p, const FineArgs&
         a.invd_sp = at(h->invd, (size_t)t * h->hm.n_sp * p.lanes);
         a.part = at(h->part, part_off);
         part_off += 2 * (size_t)nb * 3 * p.lanes;   // two buffers of 3 sums per lane and block
+        a.amg_ws = at(h->amg_ws, (size_t)t * h->amg_units * p.lanes);
         a.bar = h->bar + t;
         a.row_start = rt.rs;
         a.long_start = rt.ls;
@@ -393,6 +397,12 @@ FineArgs pppc::detail::fine_args(pppc_handle* h, double* Fout) {
         a.tri_m = h->tri_m;
         a.tri_ie = h->tri_ie;
     }
+    if (h->amg_levels > 1) {
+        a.amg = h->d_amg;
+        a.amg_levels = h->amg_levels;
+        a.amg_sweeps = kAmgCoarsestSweeps;
+        a.amg_ws = h->amg_ws;
+    }
     a.max_newton = h->cfg.max_newton;
     a.max_lin = h->cfg.max_lin;
     a.u = Fout;
@@ -538,7 +548,22 @@ pppc_status run_correct(pppc_handle* h, const double* Fl, double* Unew) {
     }
     CK(cudaGetLastError());
     TRY(reset_control(h));
-    const CocgArgs c = cocg_args(h);
+    CocgArgs c = cocg_args(h);
+    if (h->amg_levels > 1) {
+        // multigrid-preconditioned harmonic solves (precond = 2)
+        c.amg = h->d_amg;
+        c.amg_levels = h->amg_levels;
+        c.amg_sweeps = kAmgCoarsestSweeps;
+        c.amg_fp32 = h->fp32 ? 1 : 0;
+        c.amg_ws = h->camg_ws;
+        c.amg_J = h->camg_J;
+        c.amg_r = h->camg_r;
+        c.amg_z = h->camg_z;
+        c.klinP = h->fp32 ? static_cast<const void*>(h->md.Klin32) : static_cast<const void*>(h->md.Klin);
+        c.row_start = h->d_row_start;
+        c.long_start = h->d_long_start;
+        c.long_rows = h->d_long_rows;
+    }
     CK(launch_cocg(c, h->coarse_fp32, h->cocg_cfg, h->st));
     h->stats.launches += 1;
     TRY(device_status(h, "harmonic solves"));
@@ -685,6 +710,132 @@ pppc_status pppc::detail::stage_correct(pppc_handle* h, const double* Fl, double
     return run_correct(h, Fl, Unew);
 }
 
+namespace {
+
+template <typename T>
+pppc_status upload_as(pppc_handle* h, const void** out, const std::vector<double>& v) {
+    std::vector<T> c(v.begin(), v.end());
+    T* d = nullptr;
+    TRY(upload(h, &d, c));
+    *out = d;
+    return PPPC_OK;
+}
+
+// values in the fine PCG's precision
+pppc_status upload_values(pppc_handle* h, const void** out, const std::vector<double>& v) {
+    return h->fp32 ? upload_as<float>(h, out, v) : upload_as<double>(h, out, v);
+}
+
+// Multigrid preconditioner of the fine PCG (precond = 2): the representative
+// matrix A0 = J at zero field (K_lin plus the Brauer law's nu(0) = k1 + k3 on
+// the nonlinear elements, plus M / dt) is assembled by the device, the
+// hierarchy is built on the host (amg_host.cpp) and uploaded in the PCG
+// precision with one workspace region per lane team.  A mesh too small to
+// coarsen keeps amg_levels = 0 and the sweep falls back to Jacobi.
+pppc_status setup_amg(pppc_handle* h) {
+    const HostMesh& hm = h->hm;
+    h->amg_levels = 0;
+    if (hm.n_slots > 0) launch_kbar(h->md, h->N, h->NB, PPPC_COARSE_ZERO_FIELD, h->elem, h->Kbar, h->st);
+    CK(cudaGetLastError());
+    std::vector<double> klin(hm.nnz), kbar0(hm.n_slots), mslot(hm.n_slots);
+    CK(cudaMemcpyAsync(klin.data(), h->md.Klin, hm.nnz * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    if (hm.n_slots > 0) {
+        CK(cudaMemcpyAsync(kbar0.data(), h->Kbar, hm.n_slots * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaMemcpyAsync(mslot.data(), h->md.Mslot, hm.n_slots * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    std::vector<double> a0(hm.nnz);
+    for (int i = 0; i < hm.ndof; ++i)
+        for (int k = hm.rowptr[i]; k < hm.rowptr[i + 1]; ++k) {
+            const int sl = hm.row_slot[i] >= 0 ? hm.row_slot[i] + (k - hm.rowptr[i]) : -1;
+            a0[k] = sl >= 0 ? kbar0[sl] + mslot[sl] / h->dt : klin[k];
+        }
+    std::vector<AmgHostLevel> lv;
+    std::string err;
+    if (!build_amg(hm.ndof, hm.rowptr.data(), hm.col.data(), a0.data(), hm.row_slot.data(), AmgOptions{}, lv, err))
+        return fail(h, PPPC_ERR_INVALID_ARG, err);
+    if (lv.size() < 2) return PPPC_OK;
+    if ((int)lv.size() > kAmgMaxLevels) lv.resize(kAmgMaxLevels);
+    std::vector<AmgLevel> dl(lv.size());
+    long long units = 0;
+    auto take = [&](long long n) {
+        const long long o = units;
+        units += n;
+        return o;
+    };
+    h->amg_rows.clear();
+    for (size_t l = 0; l < lv.size(); ++l) {
+        const AmgHostLevel& L = lv[l];
+        AmgLevel& d = dl[l];
+        d = AmgLevel{};
+        d.n = L.n;
+        d.n_slots = L.n_slots;
+        d.n_sp = L.n_sp;
+        d.off_b = d.off_q = d.off_slot = -1;
+        h->amg_rows.push_back(L.n);
+        TRY(upload_values(h, &d.l1, L.l1));
+        if (l == 0) {
+            // the fine level's matrix is the lane's Newton matrix itself
+            d.off_y = take(L.n);
+            d.off_l1 = take(L.n_sp);
+            d.sp_index = h->md.sp_index;
+            continue;
+        }
+        d.off_slot = take(L.n_slots);
+        d.off_l1 = take(L.n_sp);
+        d.off_b = take(L.n);
+        d.off_y = take(L.n);
+        d.off_q = take(L.n);
+        int *rowptr, *col, *row_slot, *sp_index, *sp_rows, *Pptr, *Pcol, *Rptr, *Rcol, *cptr, *csrc;
+        TRY(upload(h, &rowptr, L.rowptr));
+        TRY(upload(h, &col, L.col));
+        TRY(upload(h, &row_slot, L.row_slot));
+        TRY(upload(h, &sp_index, L.sp_index));
+        TRY(upload(h, &sp_rows, L.sp_rows));
+        TRY(upload(h, &Pptr, L.Pptr));
+        TRY(upload(h, &Pcol, L.Pcol));
+        TRY(upload(h, &Rptr, L.Rptr));
+        TRY(upload(h, &Rcol, L.Rcol));
+        TRY(upload(h, &cptr, L.cptr));
+        TRY(upload(h, &csrc, L.csrc));
+        d.rowptr = rowptr;
+        d.col = col;
+        d.row_slot = row_slot;
+        d.sp_index = sp_index;
+        d.sp_rows = sp_rows;
+        d.Pptr = Pptr;
+        d.Pcol = Pcol;
+        d.Rptr = Rptr;
+        d.Rcol = Rcol;
+        d.cptr = cptr;
+        d.csrc = csrc;
+        TRY(upload_values(h, &d.val, L.val));
+        TRY(upload_values(h, &d.Pval, L.Pval));
+        TRY(upload_values(h, &d.Rval, L.Rval));
+        TRY(upload_values(h, &d.slot_base, L.slot_base));
+        TRY(upload_values(h, &d.cw, L.cw));
+    }
+    TRY(upload(h, &h->d_amg, dl));
+    const size_t ts = h->fp32 ? sizeof(float) : sizeof(double);
+    h->amg_ws = dev_alloc(h, (size_t)units * h->NB * ts);
+    if (!h->amg_ws) return fail(h, PPPC_ERR_NOMEM, "multigrid workspace allocation failed");
+    CK(cudaMemsetAsync(h->amg_ws, 0, (size_t)units * h->NB * ts, h->st));
+    // the harmonic solves' V-cycle: the same levels on 2H lanes (re, im per harmonic)
+    const size_t cl = 2 * (size_t)h->H;
+    h->camg_ws = dev_alloc(h, (size_t)units * cl * ts);
+    h->camg_J = dev_alloc(h, (size_t)std::max(hm.n_slots, 1) * cl * ts);
+    h->camg_r = dev_alloc(h, (size_t)hm.ndof * cl * ts);
+    h->camg_z = dev_alloc(h, (size_t)hm.ndof * cl * ts);
+    if (!h->camg_ws || !h->camg_J || !h->camg_r || !h->camg_z)
+        return fail(h, PPPC_ERR_NOMEM, "multigrid workspace allocation failed");
+    CK(cudaMemsetAsync(h->camg_ws, 0, (size_t)units * cl * ts, h->st));
+    h->amg_units = units;
+    h->amg_levels = (int)lv.size();
+    return PPPC_OK;
+}
+
+}  // namespace
+
 // ===========================================================================
 extern "C" {
 
@@ -738,7 +889,7 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
     else if (c.method != PPPC_METHOD_PPPC && c.method != PPPC_METHOD_PPIC) why = "unknown method";
     else if (c.coarse_at != PPPC_COARSE_AT_U && c.coarse_at != PPPC_COARSE_AT_F) why = "unknown coarse_at";
     else if (c.newton_schedule != 0 && c.newton_schedule != 1) why = "newton_schedule must be 0 or 1";
-    else if (c.precond != 0 && c.precond != 1) why = "precond must be 0 or 1";
+    else if (c.precond < 0 || c.precond > 2) why = "precond must be 0, 1 or 2";
     else if (c.predictor < 0 || c.predictor > 2) why = "predictor must be 0, 1 or 2";
     else if (c.max_newton < 1 || c.max_lin < 1 || c.max_coarse < 1) why = "iteration caps must be >= 1";
     else if (c.lane_team < -1) why = "lane_team must be -1, 0 or a lane count";
@@ -1008,14 +1159,17 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         TRY(upload(h, &h->d_row_start, rs));
         TRY(upload(h, &h->d_long_start, ls));
         TRY(upload(h, &h->d_long_rows, lrows));
+        // the team kernel's static shared memory bounds the grid-wide kernel's
+        // (same body, plus a copy of its arguments)
+        CK(fine_batch_prepare(h->fp32, &h->fine_static_smem));
         // keep p, s, x, w in shared memory when a block's rows fit
-        choose_vec_rows(h->fp32, h->NB, rows_max, (size_t)smem_optin - 1024, &h->vec_rows, &h->vec_w);
+        choose_vec_rows(h->fp32, h->NB, rows_max, (size_t)smem_optin - h->fine_static_smem - 1024, &h->vec_rows,
+                        &h->vec_w);
         CK(fine_config(h->fp32, h->NB, h->vec_rows, h->vec_w ? 4 : 3, &h->fine_cfg));
         if (h->fine_cfg.blocks != nb) return fail(h, PPPC_ERR_CUDA, "fine sweep: one block per SM expected");
         // lane teams (the plan is chosen at the first sweep)
         h->sms = nb;
         h->smem_optin = (size_t)smem_optin;
-        CK(fine_batch_prepare(h->fp32, &h->fine_static_smem));
         h->plan = pppc_fine_plan{};
         std::fill(std::begin(h->tune_ms), std::end(h->tune_ms), 0.0);
         if (h->cfg.lane_team > 0) {
@@ -1049,6 +1203,12 @@ pppc_status pppc_set_mesh(pppc_handle* h, int32_t n_nodes, const double* xy, int
         CK(cocg_config(false, 1, &h->cocg1_cfg));
     }
     CK(cudaMemsetAsync(h->counters, 0, kCounters * sizeof(long long), h->st));
+    h->amg_levels = 0;
+    h->amg_ws = nullptr;
+    h->d_amg = nullptr;
+    h->camg_ws = h->camg_J = h->camg_r = h->camg_z = nullptr;
+    h->amg_rows.clear();
+    if (h->cfg.precond == 2) TRY(setup_amg(h));
     CK(cudaStreamSynchronize(h->st));
     h->has_mesh = true;
     return PPPC_OK;
@@ -1239,6 +1399,8 @@ pppc_status pppc_get_fine_plan(pppc_handle* h, pppc_fine_plan_info* out) {
         out->candidate_lanes[c] = cand[c];
         out->candidate_ms[c] = h->tune_ms[c];
     }
+    out->amg_levels = h->amg_levels;
+    for (int l = 0; l < h->amg_levels && l < 10; ++l) out->amg_rows[l] = h->amg_rows[l];
     return PPPC_OK;
 }
 

@@ -68,6 +68,36 @@ struct SourceDev {
 // c1 = area*nu, c2 = 2*area*dnu/d(B^2), s_a = grad N_a . grad A  (a = 0,1,2)
 constexpr int kElemPlanes = 5;
 
+// One level of the fine PCG's multigrid preconditioner (precond = 2; setup
+// in amg_host.cpp).  Level 0 is the fine Newton matrix itself (the mesh's
+// CSR, per-lane special rows in FineArgs::J, shared rows K_lin); levels l >= 1
+// hold A_l = P_l^T A_{l-1} P_l for every lane: shared values on ordinary
+// rows, per-lane slots on special rows, rebuilt per Newton iteration as
+// slot_base + sum cw * (finer slots).  Vectors of a team live in its
+// workspace FineArgs::amg_ws at offsets given in units of the team's lanes.
+constexpr int kAmgMaxLevels = 10;
+struct AmgLevel {
+    int n, n_slots, n_sp, pad;
+    long long off_b, off_y, off_q, off_slot, off_l1;   // workspace offsets (x team lanes); -1 unused
+    const int* rowptr;         // l >= 1: pattern of A_l
+    const int* col;
+    const void* val;           // [nnz] shared values (T)
+    const int* row_slot;       // [n] first per-lane slot of a special row, -1 otherwise
+    const int* sp_index;       // [n] index among special rows, -1 otherwise
+    const int* sp_rows;        // [n_sp]
+    const void* l1;            // [n] sum_j |A_l(i, j)| on shared rows (T)
+    const int* Pptr;           // l >= 1: P_l, rows of level l - 1
+    const int* Pcol;
+    const void* Pval;
+    const int* Rptr;           // l >= 1: R_l = P_l^T, rows of level l
+    const int* Rcol;
+    const void* Rval;
+    const void* slot_base;     // l >= 1: [n_slots] (T)
+    const int* cptr;           // [n_slots + 1]
+    const int* csrc;           // slots of level l - 1
+    const void* cw;            // (T)
+};
+
 // Arguments of the fine sweep of one lane team: the NB lanes lane0 ..
 // lane0 + NB - 1 of a problem with N lanes.  The FP64 state vectors (u,
 // uprev, uprev2, traj*, lam_out) and the element planes are shared by all
@@ -126,6 +156,11 @@ struct FineArgs {
     const int* tri_low;      // [ndof] CSR index of entry (i, i-1), -1 if absent
     void* tri_m;             // [ndof*NB] of T: LDL^T multipliers of the chunk factorisation
     void* tri_ie;            // [ndof*NB] of T: inverse pivots
+    // multigrid preconditioner (amg != null): levels, l1-Jacobi sweeps on the
+    // coarsest level, and this team's workspace (T)
+    const AmgLevel* amg;
+    int amg_levels, amg_sweeps;
+    void* amg_ws;
 };
 
 // Device counters of a handle, accumulated over the sweeps of one call.
@@ -160,6 +195,22 @@ struct CocgArgs {
     int* status;
     long long* counters;     // [2] cocg iterations
     long long* team_ns;      // optional [2]: %globaltimer at the team's start and end
+    // multigrid preconditioner (amg != null, single-problem launches): for
+    // harmonic p the real SPD matrix S_p = Kbar + |1 - z_p| C, its V-cycle
+    // (the fine PCG's hierarchy with S_p's Galerkin coarse matrices) applied
+    // to the real and imaginary parts alike -- a real symmetric, hence
+    // complex-symmetric, preconditioner as COCG requires.  The V-cycle runs in
+    // the fine PCG's precision P on two lanes per harmonic ([row][2H] of P).
+    const AmgLevel* amg;
+    int amg_levels, amg_sweeps, amg_fp32;
+    void* amg_ws;            // [units][2H] of P
+    void* amg_J;             // [n_slots][2H] of P: S_p on the special rows
+    void* amg_r;             // [ndof][2H] of P: r converted for the V-cycle
+    void* amg_z;             // [ndof][2H] of P
+    const void* klinP;       // K_lin in P
+    const int* row_start;    // [gridDim + 1] contiguous rows of each block (the V-cycle's fine rows)
+    const int* long_start;
+    const int* long_rows;
 };
 
 }  // namespace pppc

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "amg.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -183,6 +184,73 @@ __device__ __forceinline__ void stc(T* p, cplx v) {
 
 constexpr int CNV = 5;  // per lane: |r|^2, (r,z) re/im, (z,w) re/im
 
+// |1 - z_p| for harmonic p (tw[2p] = cos, tw[2p+1] = -sin of 2 pi p / N)
+__device__ __forceinline__ double shift_abs(const double* tw, int p) {
+    const double re = 1.0 - tw[2 * p], im = -tw[2 * p + 1];
+    return sqrt(re * re + im * im);
+}
+
+// Multigrid set-up of one harmonic solve: the special rows' values of S_p
+// and their l1 norms (two lanes per harmonic), then every harmonic's coarse
+// matrices.  Called by all blocks after a barrier.
+template <typename P>
+__device__ bool cocg_amg_setup(const CocgArgs& a, const AmgLevel* lvl, int bid, int nblk) {
+    const MeshDev& m = a.mesh;
+    const int H = a.H, NB = 2 * H;
+    P* J = static_cast<P*>(a.amg_J);
+    P* l1sp = static_cast<P*>(a.amg_ws) + lvl[0].off_l1 * NB;
+    const long long items = (long long)m.n_sp * H;
+    for (long long it = bid * (long long)blockDim.x + threadIdx.x; it < items; it += (long long)nblk * blockDim.x) {
+        const int sp = (int)(it / H), p = (int)(it % H);
+        const int i = m.sp_rows[sp], kb = m.rowptr[i], ke = m.rowptr[i + 1], s0 = m.row_slot[i];
+        const double c = shift_abs(a.tw, p) * a.inv_dT;
+        P l1 = 0;
+        for (int k = kb; k < ke; ++k) {
+            const int sl = s0 + (k - kb);
+            const P v = (P)(a.Kbar[sl] + c * m.Mslot[sl]);
+            J[(size_t)sl * NB + 2 * p] = v;
+            J[(size_t)sl * NB + 2 * p + 1] = v;
+            l1 += v < (P)0 ? -v : v;
+        }
+        l1sp[(size_t)sp * NB + 2 * p] = l1;
+        l1sp[(size_t)sp * NB + 2 * p + 1] = l1;
+    }
+    if (!grid_sync(a.bar, a.status, bid, nblk)) return false;
+    const AmgCtx ctx{NB, a.amg_levels, a.amg_sweeps, a.amg_ws, a.amg_J, a.bar, a.status, a.long_start, a.long_rows};
+    return amg_coarse_values<P, 2>(ctx, lvl, bid, nblk);
+}
+
+// z = B r on the block's contiguous rows: r (FP64, final on every row: the
+// caller's barrier) converted to P, one V-cycle, z converted back.  The
+// caller's barrier publishes z.
+template <typename T, typename P>
+__device__ bool cocg_amg_apply(const CocgArgs& a, const AmgLevel* lvl, const T* r, T* z, int bid, int nblk, int RB,
+                               int rb, int pl, double* s_red, double* s_tmp) {
+    const MeshDev& m = a.mesh;
+    const int H = a.H, NB = 2 * H;
+    const int rs = a.row_start[bid], re = a.row_start[bid + 1];
+    const int l0 = 2 * pl;
+    P* rp = static_cast<P*>(a.amg_r);
+    P* zp = static_cast<P*>(a.amg_z);
+    if (rb < RB)
+        for (int i = rs + rb; i < re; i += RB) {
+            const size_t o = (size_t)i * NB + l0;
+            rp[o] = (P)r[o];
+            rp[o + 1] = (P)r[o + 1];
+        }
+    const AmgCtx ctx{NB, a.amg_levels, a.amg_sweeps, a.amg_ws, a.amg_J, a.bar, a.status, a.long_start, a.long_rows};
+    if (!amg_vcycle<P, 2>(ctx, m, lvl, static_cast<const P*>(a.klinP), static_cast<const P*>(a.amg_J), rp, zp, bid,
+                          nblk, re, rs + rb, RB, rb, l0, H, reinterpret_cast<P*>(s_red), reinterpret_cast<P*>(s_tmp)))
+        return false;
+    if (rb < RB)
+        for (int i = rs + rb; i < re; i += RB) {
+            const size_t o = (size_t)i * NB + l0;
+            z[o] = (T)zp[o];
+            z[o + 1] = (T)zp[o + 1];
+        }
+    return true;
+}
+
 // The whole solve for one team of nblk blocks (bid = this block's place in
 // it): the grid of a single-instance launch, or one member's share of a
 // batched launch.  Threads beyond the last whole row group (blockDim not a
@@ -221,6 +289,21 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
     long long iters = 0;
     if (tid == 0) s_err = 0;
     if (a.team_ns && bid == 0 && tid == 0) a.team_ns[0] = global_ns();
+    // multigrid preconditioner: level descriptors in shared memory
+    __shared__ AmgLevel s_amg[kAmgMaxLevels];
+    const bool amg = a.amg != nullptr;
+    if (amg) {
+        const int words = a.amg_levels * (int)(sizeof(AmgLevel) / sizeof(int));
+        const int* src = reinterpret_cast<const int*>(a.amg);
+        int* dst = reinterpret_cast<int*>(s_amg);
+        for (int q = tid; q < words; q += blockDim.x) dst[q] = src[q];
+        __syncthreads();
+    }
+    // z = B r with the multigrid V-cycle (after a barrier that made r final)
+    auto precondition = [&]() -> bool {
+        return a.amg_fp32 ? cocg_amg_apply<T, float>(a, s_amg, r, z, bid, nblk, RB, rb, pl, s_red, s_tmp)
+                          : cocg_amg_apply<T, double>(a, s_amg, r, z, bid, nblk, RB, rb, pl, s_red, s_tmp);
+    };
 
     // init: x = p = s = 0, r = b, z = D^-1 r
     for (int i = row0; i < m.ndof; i += rstride) {
@@ -243,6 +326,12 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
         stc<T>(z + o, cmul(iv, rv));
     }
     if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+    if (amg) {
+        const bool ok = a.amg_fp32 ? cocg_amg_setup<float>(a, s_amg, bid, nblk)
+                                   : cocg_amg_setup<double>(a, s_amg, bid, nblk);
+        if (!ok || !precondition()) return;
+        if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+    }
 
     for (int k = 0;; ++k) {
         double acc[CNV] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -350,13 +439,19 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
             const cplx sv = cadd(ldc<T>(w + o), cmul(be, ldc<T>(s + o)));
             const cplx xv = cadd(ldc<T>(x + o), cmul(al, pv));
             const cplx rv = csub(ldc<T>(r + o), cmul(al, sv));
-            const int sp = m.sp_index[i];
-            const cplx iv = sp >= 0 ? ldc<T>(invd + 2 * ((size_t)sp * H + pl)) : cplx{m.invdiag_lin[i], 0.0};
             stc<T>(p + o, pv);
             stc<T>(s + o, sv);
             stc<T>(x + o, xv);
             stc<T>(r + o, rv);
-            stc<T>(z + o, cmul(iv, rv));
+            if (!amg) {
+                const int sp = m.sp_index[i];
+                const cplx iv = sp >= 0 ? ldc<T>(invd + 2 * ((size_t)sp * H + pl)) : cplx{m.invdiag_lin[i], 0.0};
+                stc<T>(z + o, cmul(iv, rv));
+            }
+        }
+        if (amg) {
+            if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+            if (!precondition()) return;
         }
         if (!grid_sync(a.bar, a.status, bid, nblk)) return;
     }

@@ -44,8 +44,10 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "amg.cuh"
 #include "common.cuh"
 #include "kernels.h"
+#include "lanes.cuh"
 
 namespace pppc {
 
@@ -98,8 +100,6 @@ constexpr double kPi = 3.141592653589793;
 // kFloorMult of the tolerance: the residual has reached its rounding floor.
 constexpr double kStagnation = 0.5;
 constexpr double kFloorMult = 100.0;
-// Rows with more nonzeros are multiplied by the whole block (see long_rows).
-constexpr int kLongRow = 32;
 // FP32 Jacobian (mixed path): a nonlinear element whose reluctivity exceeds
 // this has its whole Jacobian contribution scaled by kNuCapFp32 / nu, which
 // keeps J symmetric positive definite and the FP32 PCG within range.  The
@@ -113,95 +113,6 @@ constexpr double kNuCapFp32 = 1e10;
 // lane reports failure (20 halvings).
 constexpr double kMinStep = 1.0 / 1048576.0;
 
-// V adjacent lanes of one row, loaded and stored as one vector access.
-template <typename T, int V>
-struct Lanes {
-    T v[V];
-};
-template <typename T, int V>
-__device__ __forceinline__ Lanes<T, V> ldv(const T* p) {
-    Lanes<T, V> r;
-    if constexpr (sizeof(T) * V == 16 && sizeof(T) == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
-        r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
-    } else {
-#pragma unroll
-        for (int h = 0; h < V; h += 2) {
-            const auto q = *reinterpret_cast<const typename vec2_t<T>::type*>(p + h);
-            r.v[h] = q.x;
-            r.v[h + 1] = q.y;
-        }
-    }
-    return r;
-}
-template <typename T, int V>
-__device__ __forceinline__ void stv(T* p, const Lanes<T, V>& x) {
-    if constexpr (sizeof(T) * V == 16 && sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
-    } else {
-#pragma unroll
-        for (int h = 0; h < V; h += 2) st2<T>(p + h, x.v[h], x.v[h + 1]);
-    }
-}
-
-// Slots of the in-block reduction scratch per value and lane: one per warp
-// when the row groups of a warp can be combined by shuffles, else one per
-// row group.
-__host__ __device__ inline int red_slots(int G, int threads) {
-    return (G < 32 && (32 % G) == 0) || G == 32 ? threads / 32 : threads / G;
-}
-
-// Fixed-order in-block reduction over the row groups of each lane, written as
-// this block's partials out[v * NB + lane].  When a
-// warp holds several row groups (G < 32 threads per row) they are first
-// combined with a fixed shuffle tree; the per-warp results are then summed in
-// warp order by one thread per (value, lane).  s_red must hold
-// NVP * (blockDim/32) * NB values (NVP * blockDim/G in the general case).
-template <typename RT, int V, int NVP>
-__device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0, RT (&v)[NVP][V], RT* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    if (G < 32 && (32 % G) == 0) {
-#pragma unroll
-        for (int q = 0; q < NVP; ++q)
-#pragma unroll
-            for (int h = 0; h < V; ++h)
-                for (int off = 16; off >= G; off >>= 1) v[q][h] += __shfl_xor_sync(0xffffffffu, v[q][h], off);
-        if (lane < G)
-#pragma unroll
-            for (int q = 0; q < NVP; ++q)
-#pragma unroll
-                for (int h = 0; h < V; ++h) s_red[(q * nwarps + warp) * NB + l0 + h] = v[q][h];
-        __syncthreads();
-        for (int o = threadIdx.x; o < NVP * NB; o += blockDim.x) {
-            const int q = o / NB, l = o - q * NB;
-            RT acc = 0;
-            for (int t = 0; t < nwarps; ++t) acc += s_red[(q * nwarps + t) * NB + l];
-            out[o] = acc;
-        }
-        return;
-    }
-    // general case: one slot per row group, pairwise tree
-    const int RB = blockDim.x / G, rb = threadIdx.x / G;
-#pragma unroll
-    for (int q = 0; q < NVP; ++q)
-#pragma unroll
-        for (int h = 0; h < V; ++h) s_red[(q * RB + rb) * NB + l0 + h] = v[q][h];
-    __syncthreads();
-    for (int n = RB; n > 1;) {
-        const int half = (n + 1) >> 1, cnt = (n - half) * NB;
-        for (int idx = threadIdx.x; idx < NVP * cnt; idx += blockDim.x) {
-            const int q = idx / cnt, rem = idx - q * cnt;
-            const int t = rem / NB, l = rem - t * NB;
-            s_red[(q * RB + t) * NB + l] += s_red[(q * RB + t + half) * NB + l];
-        }
-        __syncthreads();
-        n = half;
-    }
-    for (int o = threadIdx.x; o < NVP * NB; o += blockDim.x) {
-        const int q = o / NB, l = o - q * NB;
-        out[o] = s_red[(q * RB) * NB + l];
-    }
-}
 
 // Residual R(u) of the implicit-Euler step on this thread's rows and lanes,
 // the per-lane Jacobian values of the special rows, r = -R, z = D^-1 r and
@@ -210,7 +121,7 @@ __device__ __forceinline__ void block_partials(RT* s_red, int G, int NB, int l0,
 // (FP64 state and element data) must not constrain the PCG loops.
 template <typename T, int V>
 __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, int row0, int re, int RB, int l0,
-                                           const double* s_I, double* accR, T* accz, T* xB, size_t vo) {
+                                           const double* s_I, double* accR, T* accz, T* xB, size_t vo, T* l1sp) {
     const int NB = a.NB, LD = a.ld;
     const size_t P = (size_t)m.n_nl * LD;
     const double* u = a.u + a.lane0;
@@ -248,6 +159,9 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                     for (int h = 0; h < V; ++h) iv.v[h] = d;
                 } else {
                     double dg[V];
+                    T l1acc[V];
+#pragma unroll
+                    for (int h = 0; h < V; ++h) l1acc[h] = (T)0;
                     for (int k = kb; k < ke; ++k) {
                         const int sl = slot0 + (k - kb);
                         const int j = m.col[k];
@@ -286,7 +200,10 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
                         }
                         Lanes<T, V> jt;
 #pragma unroll
-                        for (int h = 0; h < V; ++h) jt.v[h] = (T)Jv[h];
+                        for (int h = 0; h < V; ++h) {
+                            jt.v[h] = (T)Jv[h];
+                            l1acc[h] += jt.v[h] < (T)0 ? -jt.v[h] : jt.v[h];
+                        }
                         stv<T, V>(J + (size_t)sl * NB + l0, jt);
                         if (j == i)
 #pragma unroll
@@ -295,6 +212,12 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
 #pragma unroll
                     for (int h = 0; h < V; ++h) iv.v[h] = (T)(1.0 / dg[h]);
                     stv<T, V>(invd + (size_t)m.sp_index[i] * NB + l0, iv);
+                    if (l1sp) {
+                        Lanes<T, V> lv;
+#pragma unroll
+                        for (int h = 0; h < V; ++h) lv.v[h] = l1acc[h];
+                        stv<T, V>(l1sp + (size_t)m.sp_index[i] * NB + l0, lv);
+                    }
                 }
                 const double gi = m.g[i];
                 Lanes<T, V> rv, zv, zero;
@@ -325,7 +248,7 @@ __device__ __noinline__ void residual_rows(const FineArgs& a, const MeshDev& m, 
 // b = (M/dt) lam_next + g_m.  Out of line like residual_rows.
 template <typename T, int V>
 __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, int row0, int re, int RB, int l0, int j,
-                                          double* accR, T* accz, double* accb, T* xB, size_t vo) {
+                                          double* accR, T* accz, double* accb, T* xB, size_t vo, T* l1sp) {
     const int NB = a.NB, N = a.N, LD = a.ld;
     const size_t P = (size_t)m.n_nl * LD;
     const size_t lv = (size_t)m.ndof * LD;
@@ -361,6 +284,9 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
             for (int h = 0; h < V; ++h) iv.v[h] = d;
         } else {
             double dg[V];
+            T l1acc[V];
+#pragma unroll
+            for (int h = 0; h < V; ++h) l1acc[h] = (T)0;
             for (int k = kb; k < ke; ++k) {
                 const int sl = slot0 + (k - kb);
                 const int jc = m.col[k];
@@ -419,6 +345,7 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
                     acc[h] += Jv[h] * lj.v[h] - rhs;
                     bb[h] += rhs;
                     jt.v[h] = (T)Jv[h];
+                    l1acc[h] += jt.v[h] < (T)0 ? -jt.v[h] : jt.v[h];
                 }
                 stv<T, V>(J + (size_t)sl * NB + l0, jt);
                 if (jc == i)
@@ -428,6 +355,12 @@ __device__ __noinline__ void adjoint_rows(const FineArgs& a, const MeshDev& m, i
 #pragma unroll
             for (int h = 0; h < V; ++h) iv.v[h] = (T)(1.0 / dg[h]);
             stv<T, V>(invd + (size_t)m.sp_index[i] * NB + l0, iv);
+            if (l1sp) {
+                Lanes<T, V> lv;
+#pragma unroll
+                for (int h = 0; h < V; ++h) lv.v[h] = l1acc[h];
+                stv<T, V>(l1sp + (size_t)m.sp_index[i] * NB + l0, lv);
+            }
         }
         Lanes<T, V> rv, zv, zero;
 #pragma unroll
@@ -691,6 +624,19 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
         for (size_t q = tid; q < 2 * len; q += blockDim.x) sv[q] = (T)0;   // p = s = 0
     }
     const int row0 = rs + rb;
+    // multigrid levels (precond = 2), copied to shared memory
+    __shared__ AmgLevel s_amg[kAmgMaxLevels];
+    const bool amg = a.amg != nullptr;
+    if (amg) {
+        static_assert(sizeof(AmgLevel) % sizeof(int) == 0, "AmgLevel copied as words");
+        const int words = a.amg_levels * (int)(sizeof(AmgLevel) / sizeof(int));
+        const int* src = reinterpret_cast<const int*>(a.amg);
+        int* dst = reinterpret_cast<int*>(s_amg);
+        for (int q = tid; q < words; q += blockDim.x) dst[q] = src[q];
+        __syncthreads();
+    }
+    T* l1f = amg ? static_cast<T*>(a.amg_ws) + s_amg[0].off_l1 * NB : nullptr;
+    const AmgCtx actx{NB, a.amg_levels, a.amg_sweeps, a.amg_ws, a.J, a.bar, a.status, a.long_start, a.long_rows};
     const long long n_elem_items = (long long)m.n_nl * NB;
     const long long gthreads = (long long)nblk * blockDim.x;
     // iteration counts, kept by thread 0: newton tests, pcg iterations, pcg
@@ -763,10 +709,16 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                 accz[h] = 0;
             }
             if (a.adjoint)
-                adjoint_rows<T, V>(a, m, row0, re, RB, l0, j, accR, accz, accb, xB, vo);
+                adjoint_rows<T, V>(a, m, row0, re, RB, l0, j, accR, accz, accb, xB, vo, l1f);
             else
-                residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo);
-            if (a.tri > 0) {
+                residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo, l1f);
+            if (amg) {
+                // every lane's coarse matrices from its new Jacobian, then z = B r
+                if (!grid_sync(a.bar, a.status, bid, nblk)) return;
+                if (!amg_coarse_values<T, V>(actx, s_amg, bid, nblk)) return;
+                if (!amg_vcycle<T, V>(actx, m, s_amg, KlinT, J, r, z, bid, nblk, re, row0, RB, rb, l0, G, s_red, s_tmp))
+                    return;
+            } else if (a.tri > 0) {
                 // the chunk preconditioner replaces z = D^-1 r (r of other threads' rows: sync)
                 __syncthreads();
 #pragma unroll
@@ -882,21 +834,10 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     T wv[V];
 #pragma unroll
                     for (int h = 0; h < V; ++h) wv[h] = 0;
-                    if (slot0 < 0) {
-                        for (int kk = kb; kk < ke; ++kk) {
-                            const T kv = KlinT[kk];
-                            const Lanes<T, V> zj = ldv<T, V>(z + (size_t)m.col[kk] * NB + l0);
-#pragma unroll
-                            for (int h = 0; h < V; ++h) wv[h] += kv * zj.v[h];
-                        }
-                    } else {
-                        for (int kk = kb; kk < ke; ++kk) {
-                            const Lanes<T, V> jv = ldv<T, V>(J + (size_t)(slot0 + kk - kb) * NB + l0);
-                            const Lanes<T, V> zj = ldv<T, V>(z + (size_t)m.col[kk] * NB + l0);
-#pragma unroll
-                            for (int h = 0; h < V; ++h) wv[h] += jv.v[h] * zj.v[h];
-                        }
-                    }
+                    if (slot0 < 0)
+                        gather_shared<T, V>(wv, kb, ke, m.col, KlinT, z, NB, l0);
+                    else
+                        gather_lanes<T, V>(wv, kb, ke, m.col, J, slot0, z, NB, l0);
                     const size_t o = (size_t)i * NB + l0;
                     Lanes<T, V> wl;
 #pragma unroll
@@ -1049,7 +990,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     stv<T, V>(sB + ov, sn);
                     stv<T, V>(r + o, rn);
                     stv<T, V>(xB + ov, xn);
-                    if (!tri) {
+                    if (!tri && !amg) {
                         // Jacobi: z = D^-1 r
                         Lanes<T, V> ivl, zn;
                         const int sp = m.sp_index[i];
@@ -1068,6 +1009,10 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                 if (tri) {
                     __syncthreads();   // the chunks' r were updated by other row groups
                     tri_solve<T, V>(a, rs, re, RB, rb, l0);
+                } else if (amg) {
+                    if (!amg_vcycle<T, V>(actx, m, s_amg, KlinT, J, r, z, bid, nblk, re, row0, RB, rb, l0, G, s_red,
+                                          s_tmp))
+                        return;
                 }
                 if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             }

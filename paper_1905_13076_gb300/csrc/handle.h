@@ -75,6 +75,14 @@ struct pppc_handle {
     int sms = 0;
     size_t fine_static_smem = 0, smem_optin = 0;
     double tune_ms[16] = {0};          // tuner: time of each candidate (lanes = V * 2^i), 0 if not timed
+    // multigrid preconditioner of the fine PCG (precond = 2)
+    pppc::AmgLevel* d_amg = nullptr;   // [amg_levels] level descriptors (device)
+    int amg_levels = 0;                // 0: none (precond != 2, or the mesh is too small to coarsen)
+    long long amg_units = 0;           // workspace per team, in units of the team's lanes
+    void* amg_ws = nullptr;            // [amg_units * NB] of T
+    std::vector<int> amg_rows;         // rows per level
+    // the same hierarchy preconditioning the harmonic solves: two lanes per harmonic
+    void *camg_ws = nullptr, *camg_J = nullptr, *camg_r = nullptr, *camg_z = nullptr;
     double* ext = nullptr;   // [N][n_nodes] staging for host states
     double* trace = nullptr; // Newton trace of the fine sweep (optional)
     int* trace_len = nullptr;

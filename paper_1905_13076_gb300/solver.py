@@ -58,7 +58,7 @@ class PPPC:
         cfg.method = _lib.METHODS[method]
         cfg.coarse_at = _lib.COARSE_AT[coarse_at]
         cfg.newton_schedule = int(bool(newton_schedule))
-        cfg.precond = {"jacobi": 0, "tridiag": 1}[precond]
+        cfg.precond = {"jacobi": 0, "tridiag": 1, "amg": 2}[precond]
         cfg.lane_team = int(lane_team)
         cfg.stream = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
         self.cfg = cfg
@@ -225,7 +225,8 @@ class PPPC:
         n = p.n_candidates
         return {"lanes_per_team": p.lanes_per_team, "teams": p.teams, "threads_per_row": p.threads_per_row,
                 "blocks_min": p.blocks_min, "blocks_max": p.blocks_max,
-                "candidates": list(p.candidate_lanes[:n]), "candidate_ms": list(p.candidate_ms[:n])}
+                "candidates": list(p.candidate_lanes[:n]), "candidate_ms": list(p.candidate_ms[:n]),
+                "amg_rows": list(p.amg_rows[:p.amg_levels])}
 
     def stats(self) -> dict:
         s = pppc_stats()
