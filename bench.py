@@ -1,16 +1,23 @@
 #!/usr/bin/env python3
-"""Benchmark of one PP-PC iteration (the whole hot path: batched fine
-propagators, jumps, coarse linearisation, time-axis DFT, harmonic solves,
-inverse DFT + update) on the medium coax workload: 19 801 DOFs, N = 64
-subintervals, 50 implicit-Euler steps each, Brauer steel sheath with
-sigma = 2e7 S/m, 10 A at 50 Hz.
+"""Benchmark of the PP-PC hot path (batched fine propagators, jumps, coarse
+linearisation, time-axis DFT, harmonic solves, inverse DFT + update).
 
-A "step" is one pppc_iterate() call.  value = fine DOF-steps per second
-(N * n_fine * ndof per step) over the timed steps, device time from CUDA
-events on the library's stream; L2 is flushed (512 MB write) between steps.
-Also reported: the time to periodic steady state at rel_res 1e-8 from U = 0,
+Default: the large coax workload, 499 001 DOFs, N = 256 subintervals of 200
+implicit-Euler steps, Brauer steel sheath with sigma = 3e7 S/m, 40 A at
+50 Hz + 8 A at 150 Hz, mixed precision, multigrid-preconditioned fine PCG and
+harmonic COCG.  One PP-PC iteration there takes minutes, so a "step" is a
+fixed slice of it: 2 fine levels of all 256 subintervals (continuing the
+first iteration's sweep from U = 0) plus one complete coarse update.
+value = fine DOF-steps per second (N * 2 * ndof per step) over the timed
+steps, device time from CUDA events on the library's stream; every state is
+larger than L2.  Also reported: one whole PP-PC iteration timed once, the
+time to periodic steady state at rel_res 1e-8 extrapolated from it and from
+the iteration count measured on a 50 x 100 mesh with the same time grid,
 the e2e rate through the C ABI with host buffers, the roofline of the fine
 propagator kernel, and the CPU oracle on a bounded sample.
+
+--workload medium: the medium coax workload (19 801 DOFs, N = 64, 50 fine
+steps, sigma = 2e7, 10 A at 50 Hz); a step is one pppc_iterate() call.
 
 Multi-GPU: the method runs on one GPU; with --gpus N each rank runs an
 independent replica (weak scaling, no collective on the data path).
@@ -57,6 +64,9 @@ def parse():
                     help="fine PCG preconditioner")
     ap.add_argument("--coarse-at", default="U", choices=["U", "F"],
                     help="freeze the coarse stiffness at U^k or at the fine results F^k")
+    ap.add_argument("--workload", default="large", choices=["large", "medium"],
+                    help="large: 499001 DOFs, N=256, 200 fine steps (the headline); medium: 19801 DOFs, N=64, 50")
+    ap.add_argument("--no-full", action="store_true", help="large: skip the full PP-PC iteration")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady-state run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--compare-methods", action="store_true",
@@ -361,6 +371,258 @@ def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB:
     return phase_a + phase_b + diag + matrix
 
 
+# ---- the large workload (headline) -------------------------------------------
+LARGE_LEVELS = 2   # fine implicit-Euler levels of every subinterval per timed step
+LARGE_DESC = ("coax large: nr=500 x ntheta=1000 (499001 DOFs), N=256, 200 fine steps, sigma=3e7, Brauer steel, "
+              "40 A @ 50 Hz + 8 A @ 150 Hz")
+
+
+def fine_bytes_per_row_lane_round(mixed: bool, special_frac: float, N: int, amg_rows) -> dict:
+    """Algorithmic bytes of one preconditioned PCG iteration per (row, lane)
+    of the fine propagator, FP32 vectors in the mixed path (s = 4 bytes).
+    pcg: the plain CG model, 7 s phi + 7 (s (1 - phi) + 4) / N + 13 s (matrix
+    values per lane on the special rows, shared values and indices amortised
+    over the N lanes; 13 vector passes), phi = special-row fraction.
+    vcycle: one multigrid V-cycle, on the fine level 11 vector passes (smooth:
+    read r, write y; residual: read y, r, write q; restriction reads q;
+    prolongation reads and writes y; post-smoothing reads y, r, writes z) plus
+    the per-lane Jacobian of the special rows twice and their l1 norms (16 s
+    phi), and on every coarse level 10 passes of its own length (counted
+    against the fine rows: 10 s n_l / n_0), coarse matrices not counted."""
+    s = 4.0 if mixed else 8.0
+    phi = special_frac
+    pcg = 7 * s * phi + 7 * (s * (1 - phi) + 4) / N + 13 * s
+    coarse = sum(amg_rows[1:]) / amg_rows[0] if amg_rows else 0.0
+    vcycle = 11 * s + 16 * s * phi + 10 * s * coarse if amg_rows else 0.0
+    return {"pcg": pcg, "vcycle": vcycle, "total": pcg + vcycle}
+
+
+def run_large(args, world, rank, local):
+    """The large workload: a step is LARGE_LEVELS fine implicit-Euler levels of
+    all 256 subintervals (continuing the first PP-PC iteration's fine sweep
+    from U = 0: the windows chain through the subintervals) plus one coarse
+    update (jumps, Kbar, DFT, all harmonic solves, inverse DFT + update) on
+    the fine values reached.  A whole PP-PC iteration (200 levels + coarse)
+    takes minutes here, so it is timed once beside the steps, and the time to
+    steady state is extrapolated from it."""
+    import numpy as np
+    import torch
+
+    from paper_1905_13076_gb300 import from_problem
+    from synth import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prob = workload("large")
+    mixed = args.precision == "mixed"
+    opts = dict(precision=args.precision, precond="amg", predictor=args.predictor, tol_coarse=args.tol_coarse,
+                coarse_at=args.coarse_at, stream=stream)
+    t0 = time.perf_counter()
+    s = from_problem(prob, **opts)
+    setup_s = time.perf_counter() - t0
+    N, n_nodes, ndof, nf = prob.N, prob.mesh.n_nodes, s.ndof, prob.n_fine
+    units_per_step = N * LARGE_LEVELS * ndof
+    with torch.cuda.stream(stream):
+        U0 = torch.zeros((N, n_nodes), dtype=torch.float64, device=dev)   # U^0 = 0
+    torch.cuda.synchronize(dev)
+    state = {"F": U0, "level": 0}
+
+    def step():
+        """One window of the sweep (restarting from U^0 after the last level)
+        and the coarse update of U^0 with the values reached."""
+        if state["level"] + LARGE_LEVELS > nf:
+            state["F"], state["level"] = U0, 0
+        with torch.cuda.stream(stream):
+            F = s.propagate_fine_window(state["F"], state["level"], LARGE_LEVELS)
+            a = s.stats()
+            Unew, rr = s.coarse_update(U0, F)
+            b = s.stats()
+        state["F"], state["level"] = F, state["level"] + LARGE_LEVELS
+        return {"fine_ms": a["fine_ms"], "pcg": a["pcg_iters"], "lane_rounds": a["pcg_lane_rounds"],
+                "lane_iters": a["pcg_lane_iters"], "newton": a["newton_iters"], "coarse_ms": b["coarse_ms"],
+                "cocg": b["cocg_iters"], "launches": a["launches"] + b["launches"]}
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    t0 = time.perf_counter()
+    for _ in range(max(3, args.warmup)):
+        step()
+    warmup_s = time.perf_counter() - t0
+    plan = s.fine_plan()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    per = []
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            per.append(step())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    value, t_max = aggregate(sum(step_ms), units_per_step, args.steps)
+
+    # roofline of the fine team kernel: algorithmic bytes / its event time
+    mc = s.mesh_counts()
+    bpr = fine_bytes_per_row_lane_round(mixed, mc["special_rows"] / mc["ndof"], N, plan["amg_rows"])
+    fine_s = sum(p["fine_ms"] for p in per) * 1e-3
+    lane_rounds = sum(p["lane_rounds"] for p in per)
+    alg_bytes = bpr["total"] * ndof * lane_rounds
+    hbm_peak, peak_src = peaks()
+    achieved = alg_bytes / fine_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": None, "peak_source": peak_src, "kernel": "fine_batch_kernel<float>" if mixed else
+            "fine_batch_kernel<double>", "bytes_per_row_lane_iteration": bpr,
+            "pcg_lane_iterations": lane_rounds, "kernel_seconds": fine_s}
+
+    # end to end through the C ABI with host buffers: inputs from pinned host
+    # memory every step, results read back; the same window and coarse update
+    n_e2e = min(args.steps, 3)
+    Fh = torch.empty((N, n_nodes), dtype=torch.float64).pin_memory()
+    Fh.copy_(state["F"].cpu())
+    U0h = torch.zeros((N, n_nodes), dtype=torch.float64).pin_memory()
+    lev0 = state["level"] if state["level"] + LARGE_LEVELS <= nf else 0
+    if lev0 == 0:
+        Fh.zero_()
+    e2e_t = []
+    for k in range(n_e2e):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        F2 = s.propagate_fine_window(Fh.numpy(), lev0, LARGE_LEVELS)
+        Un, rr = s.coarse_update(U0h.numpy(), F2)
+        e2e_t.append(time.perf_counter() - t0)
+    state_bytes = N * n_nodes * 8
+    e2e_value = units_per_step * n_e2e * world / sum(e2e_t)
+
+    # one whole PP-PC iteration from U = 0 (all 200 levels, then the coarse update)
+    full = None
+    if not args.no_full:
+        s.set_state(np.zeros((N, n_nodes)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        rr_full = s.iterate()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        st = s.stats()
+        full = {"seconds": e0.elapsed_time(e1) * 1e-3, "fine_s": st["fine_ms"] * 1e-3,
+                "coarse_s": st["coarse_ms"] * 1e-3, "pcg_rounds": st["pcg_iters"], "newton_rounds": st["newton_iters"],
+                "cocg_iters": st["cocg_iters"], "rel_res_of_U0": rr_full,
+                "fine_dof_steps_per_s": N * nf * ndof / (st["fine_ms"] * 1e-3 + st["coarse_ms"] * 1e-3)}
+    s.close()
+
+    # iterations to rel res 1e-8 with this time grid and excitation, measured
+    # on a 50 x 100 mesh (PP-PC's iteration count hardly depends on the mesh)
+    tts = None
+    if not args.no_tts:
+        small = workload("large", nr=50, ntheta=100)
+        with from_problem(small, precision=args.precision, precond="tridiag", predictor=args.predictor,
+                          tol_coarse=args.tol_coarse, newton_schedule=bool(args.tts_schedule),
+                          stream=stream) as ts:
+            ts.set_state(np.zeros((N, small.mesh.n_nodes)))
+            t0 = time.perf_counter()
+            iters, rr = ts.solve_periodic(tol=1e-8, kmax=60, raise_on_fail=False)
+            small_s = time.perf_counter() - t0
+        tts = {"iterations": iters, "rel_res": rr, "iterations_from": "50 x 100 mesh (4901 DOFs), same N, n_fine, "
+               "materials and excitation, inexact Newton schedule " + str(args.tts_schedule),
+               "small_mesh_seconds": small_s}
+        if full is not None:
+            # k updates need k + 1 fine sweeps and k coarse updates
+            tts["seconds_extrapolated"] = (iters + 1) * full["fine_s"] + iters * full["coarse_s"]
+            tts["label"] = "extrapolated: measured iterations x measured full-iteration times"
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu:
+        try:
+            cpu = cpu_baseline_large(cores=None)
+        except Exception as exc:
+            cpu = {"unavailable": str(exc)[:200]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": LARGE_DESC, "precision": args.precision, "parallelism": "replicas only",
+                   "step": f"{LARGE_LEVELS} fine levels of all {N} subintervals (window of the first PP-PC "
+                           "iteration's sweep from U=0) + one coarse update (jumps, Kbar, DFT, harmonic solves, "
+                           "inverse DFT)",
+                   "l2": "inputs larger than L2 (each state 1.02 GB)", "precond": "amg",
+                   "lane_team": plan["lanes_per_team"], "teams": plan["teams"], "amg_rows": plan["amg_rows"],
+                   "tol_coarse": args.tol_coarse, "predictor": args.predictor, "coarse_at": args.coarse_at},
+        "setup_s": setup_s, "warmup_s_incl_tuning": warmup_s,
+        "per_step": {k: sum(p[k] for p in per) / len(per) for k in per[0]} | {"step_ms": step_ms},
+        "full_iteration": full,
+        "time_to_steady_state": tts,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * state_bytes,
+                "d2h_bytes_per_step": 2 * state_bytes, "steps": n_e2e,
+                "calls": "pppc_propagate_fine_window + pppc_coarse_update with host arrays"},
+        "gpu_launches": sum(p["launches"] for p in per),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_large_step(n):
+    """One implicit-Euler step (Newton, sparse LU) of subinterval n of the
+    large workload from rest: the oracle's first fine level (a pool worker)."""
+    import numpy as np
+
+    from oracle.fem import FEModel
+    from oracle.stepping import ie_step
+    from synth import workload
+
+    prob = workload("large")
+    m = _oracle_large_step.model = getattr(_oracle_large_step, "model", None) or FEModel(prob)
+    dt = prob.T / (prob.N * prob.n_fine)
+    t0 = time.perf_counter()
+    ie_step(m, np.zeros(m.ndof), ((n - 1) * prob.n_fine + 1) * dt, dt)
+    return m.ndof, time.perf_counter() - t0
+
+
+def cpu_baseline_large(cores=None, pool=None):
+    """The FP64 oracle as it stands on every host core, on a bounded sample of
+    the large workload: the first implicit-Euler step of one subinterval per
+    core (one sparse LU of 499 001 unknowns per Newton iteration), each
+    process single-threaded.  The rate is the summed work over the longest
+    step; building the FE model is not timed."""
+    import multiprocessing as mp
+
+    cores = max(1, min(cores or os.cpu_count() or 1, 256))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        own = pool is None
+        if own:
+            pool = mp.get_context("spawn").Pool(cores)
+        try:
+            res = pool.map_async(_oracle_large_step, list(range(1, cores + 1)), chunksize=1).get(timeout=900)
+        finally:
+            if own:
+                pool.close()
+                pool.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    units = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": units / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} subintervals x 1 implicit-Euler/Newton step with sparse LU on 499001 DOFs, "
+                      f"one single-threaded process per core, from rest ({wall:.1f} s, the longest of them)"}
+
+
 def cpu_baseline(prob, max_seconds=20.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     fine propagators of whole subintervals from rest (Eqs. 2-3), one core."""
@@ -466,11 +728,37 @@ def dist_init():
 
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle timed as it stands on the host's cores
-    (rank 0 only): each step runs one subinterval's fine propagator per core
-    in a process pool; the value is the median over the steps."""
+    (rank 0 only): each step runs, in a process pool, one subinterval's fine
+    propagation per core (large: the first implicit-Euler step; medium: the
+    whole subinterval); the value is the median over the steps."""
     if rank != 0:
         return
     from synth import workload
+
+    if args.workload == "large":
+        import multiprocessing as mp
+
+        t_all = time.perf_counter()
+        cores = max(1, min(os.cpu_count() or 1, 256))
+        vals, base = [], None
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        with mp.get_context("spawn").Pool(cores) as pool:
+            for _ in range(max(1, args.steps)):
+                base = cpu_baseline_large(cores, pool=pool)
+                vals.append(base["value"])
+        value = statistics.median(vals)
+        base["value"] = value
+        base["sample"] += f"; median of {len(vals)} such samples"
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": LARGE_DESC, "parallelism": "replicas only"},
+                "cpu_baseline": base,
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": time.perf_counter() - t_all}
+        print(json.dumps(line))
+        return
 
     prob = workload(WORKLOAD)
     for _ in range(args.warmup):
@@ -513,6 +801,9 @@ def main():
     if args.adjoint:
         if rank == 0:
             run_adjoint(args, local)
+        return
+    if args.workload == "large":
+        run_large(args, world, rank, local)
         return
     import numpy as np
     import torch

@@ -76,3 +76,20 @@ def test_pcg_bytes_model_counts_the_tridiagonal_extras():
     tri = bench.pcg_bytes_per_row_lane(True, 0.13, 6.9, 64, tri=True)
     assert 60 < jac < 90 and tri > jac
     assert bench.pcg_bytes_per_row_lane(False, 0.13, 6.9, 64) > jac      # FP64 vectors
+
+
+def test_fine_byte_model_plain_cg_part_is_the_scope_model():
+    """The plain CG part of the bench's per-(row, lane, iteration) byte model
+    is 7 s phi + 7 (s (1 - phi) + 4) / N + 13 s: 56.5 B in FP32 for the medium
+    workload (phi = 2600 / 19801 special rows, N = 64).  The V-cycle adds 11
+    fine-level vector passes, the special rows' Jacobian twice with their l1
+    norms, and 10 passes per coarse level scaled by its length."""
+    import bench
+
+    b = bench.fine_bytes_per_row_lane_round(True, 2600 / 19801, 64, [])
+    assert abs(b["pcg"] - 56.49) < 0.01 and b["vcycle"] == 0.0
+    rows = [19801, 4488, 739, 148]
+    b = bench.fine_bytes_per_row_lane_round(True, 2600 / 19801, 64, rows)
+    coarse = sum(rows[1:]) / rows[0]
+    assert abs(b["vcycle"] - (44 + 64 * 2600 / 19801 + 40 * coarse)) < 1e-9
+    assert b["total"] == b["pcg"] + b["vcycle"]
