@@ -60,7 +60,7 @@ def parse():
                          "side is the jumps, so a relative tolerance shrinks the absolute error with them)")
     ap.add_argument("--predictor", type=int, default=2, choices=[0, 1, 2],
                     help="Newton start: 0 previous level, 1 linear, 2 quadratic extrapolation")
-    ap.add_argument("--precond", default="tridiag", choices=["jacobi", "tridiag"],
+    ap.add_argument("--precond", default="tridiag", choices=["jacobi", "tridiag", "amg"],
                     help="fine PCG preconditioner")
     ap.add_argument("--coarse-at", default="U", choices=["U", "F"],
                     help="freeze the coarse stiffness at U^k or at the fine results F^k")
@@ -68,6 +68,11 @@ def parse():
                     help="large: 499001 DOFs, N=256, 200 fine steps (the headline); medium: 19801 DOFs, N=64, 50")
     ap.add_argument("--no-full", action="store_true", help="large: skip the full PP-PC iteration")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady-state run")
+    ap.add_argument("--profile-case", default=None, choices=["medium-short", "midsize"],
+                    help="instead of the benchmark: a short case for ncu captures (medium-short: the medium mesh "
+                         "with 2 fine steps, two PP-PC iterations from rest; midsize: a 250 x 500 mesh (124 501 "
+                         "DOFs) with N=256, one fine level of every subinterval and one coarse update, states "
+                         "larger than L2); fixed lane split, so no tuning launches")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--compare-methods", action="store_true",
                     help="instead of the benchmark: PP-PC vs PP-IC iterations to 1e-6 on the paper-shaped case")
@@ -481,6 +486,28 @@ def run_large(args, world, rank, local):
             "fine_batch_kernel<double>", "bytes_per_row_lane_iteration": bpr,
             "pcg_lane_iterations": lane_rounds, "kernel_seconds": fine_s}
 
+    # parity at full size on sampled outputs: one fine level of two
+    # subintervals (where the current is high) from rest, against the
+    # oracle's implicit-Euler/Newton step with sparse LU
+    parity = None
+    if not args.no_cpu:
+        with torch.cuda.stream(stream):
+            F1 = s.propagate_fine_window(U0, 0, 1)
+        F1h = F1.cpu().numpy()
+        free = prob.mesh.dirichlet == 0
+        lanes = (64, 200)
+        try:
+            import multiprocessing as mp
+
+            with mp.get_context("spawn").Pool(len(lanes)) as pool:
+                ref = pool.map_async(_oracle_large_level1, [n + 1 for n in lanes], chunksize=1).get(timeout=900)
+            errs = {n: float(np.linalg.norm(F1h[n][free] - u) / np.linalg.norm(u)) for n, u in zip(lanes, ref)}
+            parity = {"fine_level_rel_err": max(errs.values()), "per_lane": errs,
+                      "tol": 1e-7 if mixed else 1e-9,
+                      "what": "level 1 of subintervals 65 and 201 from U=0 vs the oracle's Newton step (sparse LU)"}
+        except Exception as exc:
+            parity = {"unavailable": str(exc)[:200]}
+
     # end to end through the C ABI with host buffers: inputs from pinned host
     # memory every step, results read back; the same window and coarse update
     n_e2e = min(args.steps, 3)
@@ -560,6 +587,7 @@ def run_large(args, world, rank, local):
         "per_step": {k: sum(p[k] for p in per) / len(per) for k in per[0]} | {"step_ms": step_ms},
         "full_iteration": full,
         "time_to_steady_state": tts,
+        "error_vs_oracle": parity,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * state_bytes,
                 "d2h_bytes_per_step": 2 * state_bytes, "steps": n_e2e,
@@ -586,6 +614,22 @@ def _oracle_large_step(n):
     t0 = time.perf_counter()
     ie_step(m, np.zeros(m.ndof), ((n - 1) * prob.n_fine + 1) * dt, dt)
     return m.ndof, time.perf_counter() - t0
+
+
+def _oracle_large_level1(n):
+    """The oracle's first implicit-Euler step of subinterval n of the large
+    workload from rest (free nodes)."""
+    import numpy as np
+
+    from oracle.fem import FEModel
+    from oracle.stepping import ie_step
+    from synth import workload
+
+    prob = workload("large")
+    m = FEModel(prob)
+    dt = prob.T / (prob.N * prob.n_fine)
+    u, _ = ie_step(m, np.zeros(m.ndof), ((n - 1) * prob.n_fine + 1) * dt, dt)
+    return u
 
 
 def cpu_baseline_large(cores=None, pool=None):
@@ -738,18 +782,24 @@ def run_reference(args, world, rank):
     if args.workload == "large":
         import multiprocessing as mp
 
+        # each step is one implicit-Euler step of one subinterval (one sparse
+        # LU of 499 001 unknowns per Newton iteration, ~20-100 s); the K steps
+        # run concurrently on the host cores, one single-threaded process each
         t_all = time.perf_counter()
-        cores = max(1, min(os.cpu_count() or 1, 256))
-        vals, base = [], None
+        K = max(1, args.steps)
+        cores = max(1, min(os.cpu_count() or 1, K))
         for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ[k] = "1"
         with mp.get_context("spawn").Pool(cores) as pool:
-            for _ in range(max(1, args.steps)):
-                base = cpu_baseline_large(cores, pool=pool)
-                vals.append(base["value"])
-        value = statistics.median(vals)
-        base["value"] = value
-        base["sample"] += f"; median of {len(vals)} such samples"
+            t0 = time.perf_counter()
+            res = pool.map_async(_oracle_large_step, [1 + (7 * j) % 256 for j in range(K)], chunksize=1).get(
+                timeout=3000)
+            wall = time.perf_counter() - t0
+        value = sum(r[0] for r in res) / wall
+        base = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{K} implicit-Euler/Newton steps with sparse LU on 499001 DOFs (one per timed step, "
+                          f"subintervals spread over the period, from rest) on {cores} single-threaded processes "
+                          f"({wall:.1f} s in all, building the FE models included)"}
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -784,9 +834,39 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def profile_case(args):
+    """Short runs for ncu captures (see --profile-case); prints their counts."""
+    import numpy as np
+
+    from paper_1905_13076_gb300 import from_problem
+    from synth import workload
+
+    if args.profile_case == "medium-short":
+        prob = workload("medium", n_fine=2)
+        with from_problem(prob, precision=args.precision, precond=args.precond, lane_team=32, predictor=2,
+                          tol_coarse=args.tol_coarse) as s:
+            s.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
+            for _ in range(2):
+                rr = s.iterate()
+                print(json.dumps({"case": args.profile_case, "rel_res": rr} | s.stats()), flush=True)
+        return
+    prob = workload("large", nr=250, ntheta=500)
+    with from_problem(prob, precision=args.precision, precond="amg", lane_team=16, predictor=2,
+                      tol_coarse=args.tol_coarse) as s:
+        U = np.zeros((prob.N, prob.mesh.n_nodes))
+        F = s.propagate_fine_window(U, 0, 1)
+        print(json.dumps({"case": args.profile_case, "window": 1} | s.stats()), flush=True)
+        Un, rr = s.coarse_update(U, F)
+        print(json.dumps({"case": args.profile_case, "coarse": 1, "rel_res": rr} | s.stats()), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
+    if args.profile_case:
+        if rank == 0:
+            profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

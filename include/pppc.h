@@ -175,6 +175,9 @@ typedef struct pppc_stats {
     int64_t pcg_lane_iters;  /* sum over subintervals of the PCG iterations each one needed;
                                 1 - pcg_lane_iters / pcg_lane_rounds is the lockstep idle share */
     int64_t newton_lane_rounds; /* sum over lane teams of Newton rounds x lanes per team */
+    int64_t graph_launches;  /* CUDA graph launches: with PPPC_METHOD_PPPC and no trace, every
+                                iterate / solve iteration is one captured graph (fine sweep, jumps,
+                                Kbar, DFT, harmonic solves, inverse DFT + update) and one host sync */
 } pppc_stats;
 
 /* Fill *cfg with defaults: T=0.02, N=16, n_fine=20, FP64, averaged Jacobian,

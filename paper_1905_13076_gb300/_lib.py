@@ -56,6 +56,7 @@ class pppc_stats(ctypes.Structure):
         ("fine_steps", c_int64), ("pppc_iters", c_int32), ("rel_res", c_double),
         ("fine_ms", c_double), ("coarse_ms", c_double), ("launches", c_int64), ("backtracks", c_int64),
         ("pcg_lane_rounds", c_int64), ("pcg_lane_iters", c_int64), ("newton_lane_rounds", c_int64),
+        ("graph_launches", c_int64),
     ]
 
 

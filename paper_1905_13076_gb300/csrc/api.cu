@@ -81,6 +81,14 @@ void* dev_alloc(pppc_handle* h, size_t bytes) {
 
 void free_all(pppc_handle* h) {
     if (h->st) cudaStreamSynchronize(h->st);
+    if (h->gst) cudaStreamSynchronize(h->gst);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->graph_dirty = true;
+    h->d_ctl_in = nullptr;   // freed with the other workspace below
+    h->d_ctl = nullptr;
+    h->d_graph_args = nullptr;
+    h->d_graph_map = nullptr;
     for (void* ptr : h->allocs) {
         if (h->cfg.free_fn)
             h->cfg.free_fn(ptr, h->cfg.alloc_ctx);
@@ -214,15 +222,16 @@ pppc_status make_plan(pppc_handle* h, int lanes, pppc_fine_plan* p) {
     return PPPC_OK;
 }
 
-// Launch the sweep `base` (one team over all lanes) as the teams of plan p:
+// The sweep `base` (one team over all lanes) as the teams of plan p:
 // per-team arguments with the team's lanes, its regions of the PCG vectors
-// and partial sums, its barrier and its row partition.
-pppc_status launch_plan(pppc_handle* h, const pppc_fine_plan& p, const FineArgs& base) {
+// and partial sums, its barrier and its row partition, and the block map.
+void team_tables(pppc_handle* h, const pppc_fine_plan& p, const FineArgs& base, std::vector<FineArgs>& args,
+                 std::vector<int4>& map) {
     const size_t ts = h->fp32 ? sizeof(float) : sizeof(double);
     const size_t ndof = h->hm.ndof;
     auto at = [&](void* b, size_t elems) -> void* { return b ? static_cast<char*>(b) + elems * ts : nullptr; };
-    std::vector<FineArgs> args(p.teams);
-    std::vector<int4> map(h->sms, make_int4(-1, 0, 0, 0));
+    args.assign(p.teams, FineArgs{});
+    map.assign(h->sms, make_int4(-1, 0, 0, 0));
     const size_t budget = h->smem_optin - h->fine_static_smem - 1024;
     size_t part_off = 0;
     int first = 0;
@@ -258,6 +267,13 @@ pppc_status launch_plan(pppc_handle* h, const pppc_fine_plan& p, const FineArgs&
         for (int k = 0; k < nb; ++k) map[first + k] = make_int4(t, k, nb, 0);
         first += nb;
     }
+}
+
+// Launch the sweep `base` as the teams of plan p.
+pppc_status launch_plan(pppc_handle* h, const pppc_fine_plan& p, const FineArgs& base) {
+    std::vector<FineArgs> args;
+    std::vector<int4> map;
+    team_tables(h, p, base, args, map);
     CK(cudaMemcpyAsync(h->d_team_args, args.data(), args.size() * sizeof(FineArgs), cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->d_team_map, map.data(), map.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
     CK(launch_fine_batch(h->d_team_args, h->d_team_map, h->fp32, h->sms, p.smem, h->st));
@@ -539,6 +555,8 @@ pppc_status run_kbar(pppc_handle* h, const double* state) {
     return PPPC_OK;
 }
 
+CocgArgs single_cocg_args(pppc_handle* h);
+
 // Unew = Fl (shifted) + the harmonic correction from the jumps in h->d and
 // the current Kbar (Eqs. 11-14 in delta form).
 pppc_status run_correct(pppc_handle* h, const double* Fl, double* Unew) {
@@ -548,6 +566,19 @@ pppc_status run_correct(pppc_handle* h, const double* Fl, double* Unew) {
     }
     CK(cudaGetLastError());
     TRY(reset_control(h));
+    const CocgArgs c = single_cocg_args(h);
+    CK(launch_cocg(c, h->coarse_fp32, h->cocg_cfg, h->st));
+    h->stats.launches += 1;
+    TRY(device_status(h, "harmonic solves"));
+    launch_idft_update(h->hm.ndof, h->N, h->NB, h->H, h->coarse_fp32, h->cx, Fl, h->tw, Unew, h->st);
+    h->stats.launches += 1;
+    CK(cudaGetLastError());
+    return PPPC_OK;
+}
+
+// Arguments of h's own harmonic solves: the batched COCG over all harmonics,
+// multigrid-preconditioned with precond = 2.
+CocgArgs single_cocg_args(pppc_handle* h) {
     CocgArgs c = cocg_args(h);
     if (h->amg_levels > 1) {
         // multigrid-preconditioned harmonic solves (precond = 2)
@@ -564,13 +595,7 @@ pppc_status run_correct(pppc_handle* h, const double* Fl, double* Unew) {
         c.long_start = h->d_long_start;
         c.long_rows = h->d_long_rows;
     }
-    CK(launch_cocg(c, h->coarse_fp32, h->cocg_cfg, h->st));
-    h->stats.launches += 1;
-    TRY(device_status(h, "harmonic solves"));
-    launch_idft_update(h->hm.ndof, h->N, h->NB, h->H, h->coarse_fp32, h->cx, Fl, h->tw, Unew, h->st);
-    h->stats.launches += 1;
-    CK(cudaGetLastError());
-    return PPPC_OK;
+    return c;
 }
 
 // Unew = coarse-corrected state from Ul, Fl and the jumps in h->d.
@@ -651,6 +676,151 @@ pppc_status run_update(pppc_handle* h, const double* Ul, const double* Fl, doubl
 void swap_state(pppc_handle* h) {
     std::swap(h->U, h->Unext);
     if (h->cfg.method == PPPC_METHOD_PPIC) std::swap(h->UN, h->UNnext);
+    h->graph_dirty = true;   // a captured iteration holds the state's address
+}
+
+// ---- one PP-PC iteration as one captured CUDA graph -------------------------
+
+bool graph_eligible(const pppc_handle* h) { return h->cfg.method == PPPC_METHOD_PPPC && h->trace_cap == 0; }
+
+void destroy_graph(pppc_handle* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->graph_dirty = true;
+}
+
+// Capture errors end the capture before returning.
+#define GCAP(call)                                                                          \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            cudaGraph_t g_ = nullptr;                                                       \
+            cudaStreamEndCapture(h->gst, &g_);                                              \
+            if (g_) cudaGraphDestroy(g_);                                                   \
+            cudaGetLastError();                                                             \
+            return fail(h, PPPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                   \
+    } while (0)
+
+// Capture U -> F (fine sweep, the handle's lane-team plan), jumps, Kbar,
+// right-hand side + DFT, harmonic solves, inverse DFT + update into Unext,
+// the commit of Unext into U and the control block, on the handle's graph
+// stream.  The Newton tolerance and the commit threshold are read from
+// d_ctl_in, which the graph's first node fills from pinned ctl_in.
+pppc_status capture_iteration(pppc_handle* h) {
+    destroy_graph(h);
+    if (!h->gst) CK(cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking));
+    if (!h->gev) CK(cudaEventCreate(&h->gev));
+    if (!h->ctl_in) {
+        CK(cudaMallocHost(&h->ctl_in, 2 * sizeof(double)));
+        CK(cudaMallocHost(&h->ctl_out, sizeof(IterCtl)));
+    }
+    if (!h->d_ctl_in) {
+        TRY(alloc_n(h, &h->d_ctl_in, 2));
+        TRY(alloc_n(h, &h->d_ctl, 1));
+        TRY(alloc_n(h, &h->d_graph_args, kMaxTeams));
+        TRY(alloc_n(h, &h->d_graph_map, (size_t)h->sms));
+    }
+    FineArgs a = fine_args(h, h->F);
+    a.tol_abs_dev = h->d_ctl_in;
+    const bool one_team = h->plan.lanes < 0;
+    if (!one_team) {
+        std::vector<FineArgs> args;
+        std::vector<int4> map;
+        team_tables(h, h->plan, a, args, map);
+        CK(cudaMemcpyAsync(h->d_graph_args, args.data(), args.size() * sizeof(FineArgs), cudaMemcpyHostToDevice,
+                           h->st));
+        CK(cudaMemcpyAsync(h->d_graph_map, map.data(), map.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    const CocgArgs c = single_cocg_args(h);
+    const int ndof = h->hm.ndof, N = h->N, NB = h->NB;
+    const size_t lane_bytes = (size_t)ndof * NB * sizeof(double);
+    int kernels = 0;
+    CK(cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal));
+    GCAP(cudaMemcpyAsync(h->d_ctl_in, h->ctl_in, 2 * sizeof(double), cudaMemcpyHostToDevice, h->gst));
+    GCAP(cudaMemsetAsync(h->status, 0, sizeof(int), h->gst));
+    GCAP(cudaMemsetAsync(h->bar, 0, kMaxTeams * sizeof(GridBarrier), h->gst));
+    GCAP(reset_team_ctl(h, h->gst));
+    GCAP(cudaMemcpyAsync(h->F, h->U, lane_bytes, cudaMemcpyDeviceToDevice, h->gst));
+    GCAP(cudaEventRecordWithFlags(h->ev[0], h->gst, cudaEventRecordExternal));
+    if (one_team)
+        GCAP(launch_fine_sweep(a, h->fp32, h->fine_cfg, h->gst));
+    else
+        GCAP(launch_fine_batch(h->d_graph_args, h->d_graph_map, h->fp32, h->sms, h->plan.smem, h->gst));
+    kernels += 1;
+    GCAP(cudaEventRecordWithFlags(h->ev[1], h->gst, cudaEventRecordExternal));
+    launch_jumps(ndof, N, NB, h->U, h->F, h->d, h->part, h->jsums, h->gst);
+    kernels += 2;
+    const int lin = h->cfg.coarse_lin;
+    if (lin != PPPC_COARSE_ZERO_FIELD && h->md.n_nl > 0) {
+        launch_elem_data(h->md, NB, h->cfg.coarse_at == PPPC_COARSE_AT_F ? h->F : h->U, h->elem, h->gst);
+        kernels += 1;
+    }
+    if (h->md.n_slots > 0) {
+        launch_kbar(h->md, N, NB, lin, h->elem, h->Kbar, h->gst);
+        kernels += 1;
+    }
+    if (h->md.n_sp > 0) {
+        launch_coarse_rhs(h->md, N, NB, h->H, 1.0 / h->dT, h->d, h->tw, h->y, h->b, h->gst);
+        kernels += 2;
+    }
+    GCAP(cudaGetLastError());
+    GCAP(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), h->gst));   // the harmonic solves' barrier; status kept
+    GCAP(launch_cocg(c, h->coarse_fp32, h->cocg_cfg, h->gst));
+    launch_idft_update(ndof, N, NB, h->H, h->coarse_fp32, h->cx, h->F, h->tw, h->Unext, h->gst);
+    launch_commit((long long)ndof * NB, h->status, h->jsums, h->d_ctl_in + 1, h->Unext, h->U, h->counters, h->d_ctl,
+                  h->gst);
+    kernels += 4;
+    GCAP(cudaGetLastError());
+    GCAP(cudaEventRecordWithFlags(h->ev[3], h->gst, cudaEventRecordExternal));
+    GCAP(cudaMemcpyAsync(h->ctl_out, h->d_ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, h->gst));
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamEndCapture(h->gst, &g));
+    const cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    h->graph_kernels = kernels;
+    h->graph_dirty = false;
+    return PPPC_OK;
+}
+
+// One PP-PC iteration through the graph: U^{k+1} replaces U^k unless
+// rel_res(U^k) <= tol_commit.  *rr receives rel_res(U^k).  One host sync.
+pppc_status run_graph_iteration(pppc_handle* h, double tol_commit, double* rr) {
+    TRY(choose_plan(h, h->U, h->F));   // a first sweep tunes the lane split outside any graph
+    if (h->graph_dirty || !h->gexec) TRY(capture_iteration(h));
+    h->ctl_in[0] = fine_args(h, h->F).tol_abs;   // the inexact schedule's Newton tolerance
+    h->ctl_in[1] = tol_commit;
+    CK(cudaStreamSynchronize(h->st));          // the caller's work on its stream comes first
+    CK(cudaEventRecord(h->ev[2], h->gst));
+    CK(cudaGraphLaunch(h->gexec, h->gst));
+    CK(cudaEventRecord(h->gev, h->gst));
+    CK(cudaStreamSynchronize(h->gst));
+    h->stats.launches += h->graph_kernels;
+    h->stats.graph_launches += 1;
+    // fine and coarse device time from the graph's event nodes; if those
+    // cannot be read, the whole launch counts as fine time
+    float fms = 0.f, cms = 0.f;
+    if (cudaEventElapsedTime(&fms, h->ev[0], h->ev[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&cms, h->ev[1], h->ev[3]) == cudaSuccess) {
+        h->stats.fine_ms += fms;
+        h->stats.coarse_ms += cms;
+    } else {
+        cudaGetLastError();
+        CK(cudaEventElapsedTime(&fms, h->ev[2], h->gev));
+        h->stats.fine_ms += fms;
+    }
+    const IterCtl& o = *h->ctl_out;
+    if (o.status != 0) {
+        TRY(device_status(h, "PP-PC iteration"));
+        return fail(h, PPPC_ERR_CUDA, "PP-PC iteration: device status " + std::to_string(o.status));
+    }
+    const double dd = o.jsums[0], ff = o.jsums[1];
+    if (!std::isfinite(dd) || !std::isfinite(ff)) return fail(h, PPPC_ERR_NAN, "non-finite jump norm");
+    *rr = ff > 0.0 ? std::sqrt(dd / ff) : (dd > 0.0 ? INFINITY : 0.0);
+    h->stats.rel_res = *rr;
+    return PPPC_OK;
 }
 
 pppc_status begin_call(pppc_handle* h) {
@@ -915,6 +1085,10 @@ pppc_status pppc_create(const pppc_config* cfg, pppc_handle** out) {
 void pppc_destroy(pppc_handle* h) {
     if (!h) return;
     free_all(h);
+    if (h->gst) cudaStreamDestroy(h->gst);
+    if (h->gev) cudaEventDestroy(h->gev);
+    if (h->ctl_in) cudaFreeHost(h->ctl_in);
+    if (h->ctl_out) cudaFreeHost(h->ctl_out);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     delete h;
@@ -1299,6 +1473,16 @@ pppc_status pppc_coarse_update(pppc_handle* h, const double* U, const double* F,
 pppc_status pppc_iterate(pppc_handle* h, double* rel_res) {
     TRY(need_ready(h));
     TRY(begin_call(h));
+    if (graph_eligible(h)) {
+        double rr = 0.0;
+        TRY(run_graph_iteration(h, -1.0, &rr));   // always commit U^{k+1}
+        if (rel_res) *rel_res = rr;
+        h->rr_prev = rr;
+        TRY(end_call(h));
+        h->stats.fine_steps = h->cfg.n_fine;
+        h->stats.pppc_iters = 1;
+        return PPPC_OK;
+    }
     TRY(run_fine(h, h->U, h->F));
     TRY(run_jumps(h, h->U, h->F, rel_res));
     h->rr_prev = h->stats.rel_res;
@@ -1316,6 +1500,22 @@ pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_
     if (!(tol > 0.0) || kmax < 0) return fail(h, PPPC_ERR_INVALID_ARG, "tol must be > 0 and kmax >= 0");
     TRY(begin_call(h));
     double rr = INFINITY;
+    for (int k = 0; graph_eligible(h); ++k) {
+        // the update is committed on the device only while rel_res > tol and k < kmax
+        TRY(run_graph_iteration(h, k >= kmax ? INFINITY : tol, &rr));
+        h->rr_prev = rr;
+        h->stats.fine_steps += h->cfg.n_fine;
+        if (rr <= tol || k >= kmax) {
+            if (iters) *iters = k;
+            if (rel_res) *rel_res = rr;
+            h->stats.pppc_iters = k;
+            TRY(end_call(h));
+            h->stats.rel_res = rr;
+            if (rr <= tol) return PPPC_OK;
+            return fail(h, PPPC_ERR_NOT_CONVERGED,
+                        "rel_res " + std::to_string(rr) + " > tol after " + std::to_string(k) + " updates");
+        }
+    }
     for (int k = 0;; ++k) {
         TRY(run_fine(h, h->U, h->F));
         TRY(run_jumps(h, h->U, h->F, &rr));

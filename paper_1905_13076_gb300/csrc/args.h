@@ -115,6 +115,7 @@ struct FineArgs {
                              // (lane l's step s ends at t = (l n_total + level0 + s + 1) dt)
     double dt, inv_dt;
     double tol_abs;          // Newton stop on ||R||_2 per lane
+    const double* tol_abs_dev; // if not null: read the Newton stop from here at launch (captured graphs)
     double tol_lin;          // smallest PCG forcing term
     int max_newton, max_lin;
     double* u;               // [ndof*NB] Newton state in, F_n out (FP64)
@@ -173,6 +174,14 @@ constexpr int kCntPcgLaneRounds = 4; // sum over teams of PCG rounds x team lane
 constexpr int kCntPcgLaneIters = 5;  // sum over lanes of the PCG iterations that lane needed
 constexpr int kCntNewtonLaneRounds = 6;  // sum over teams of Newton rounds x team lanes
 constexpr int kMaxTeams = 256;       // lane teams of one sweep (at most one block each)
+
+// Control block of one captured PP-PC iteration, gathered on the device and
+// copied to pinned host memory by the graph's last node.
+struct IterCtl {
+    long long status;
+    double jsums[2];              // ||d||^2, ||F||^2
+    long long counters[kCounters];
+};
 
 // One record per Newton test of the fine sweep:
 // step, Newton iteration, max over lanes of ||R||_2, lanes still iterating,

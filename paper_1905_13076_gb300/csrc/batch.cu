@@ -122,13 +122,20 @@ pppc_status bfail(pppc_batch* b, pppc_status s, const std::string& msg) {
         if (s_ != PPPC_OK) return s_;  \
     } while (0)
 
+// Batch tables come from the members' allocator (pppc_config.alloc of the
+// first member, e.g. PyTorch's caching allocator), else cudaMalloc.
 template <typename T>
 pppc_status balloc(pppc_batch* b, T** out, size_t n) {
     void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    const pppc_config& c = b->m[0]->cfg;
+    if (c.alloc) {
+        p = c.alloc(bytes, c.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
-        return bfail(b, PPPC_ERR_NOMEM, "batch table allocation failed");
+        p = nullptr;
     }
+    if (!p) return bfail(b, PPPC_ERR_NOMEM, "batch table allocation failed");
     b->allocs.push_back(p);
     *out = static_cast<T*>(p);
     return PPPC_OK;
@@ -461,7 +468,13 @@ void pppc_batch_destroy(pppc_batch* b) {
     if (b->st) cudaStreamSynchronize(b->st);
     destroy_graphs(b);
     if (b->st) cudaStreamDestroy(b->st);
-    for (void* p : b->allocs) cudaFree(p);
+    for (void* p : b->allocs) {
+        const pppc_config& c = b->m[0]->cfg;
+        if (c.free_fn)
+            c.free_fn(p, c.alloc_ctx);
+        else
+            cudaFree(p);
+    }
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);

@@ -591,6 +591,40 @@ __global__ void lanes_to_state_kernel(int n_nodes, int N, int NB, const int* dof
 
 }  // namespace
 
+namespace {
+
+// Last kernels of a captured PP-PC iteration: U = Unext unless an error was
+// flagged or the jumps met tol_commit (rel_res <= tol_commit keeps U^k, the
+// iterate that passed); then the control block for the host.
+__global__ void commit_kernel(long long total, const int* status, const double* jsums, const double* tol_commit,
+                              const double* Unext, double* U) {
+    if (*status != 0) return;
+    const double dd = jsums[0], ff = jsums[1];
+    const double rr = ff > 0.0 ? sqrt(dd / ff) : (dd > 0.0 ? INFINITY : 0.0);
+    if (!(rr > *tol_commit)) return;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total;
+         it += (long long)gridDim.x * blockDim.x)
+        U[it] = Unext[it];
+}
+
+__global__ void iter_ctl_kernel(const int* status, const double* jsums, const long long* counters, IterCtl* out) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        out->status = *status;
+        out->jsums[0] = jsums[0];
+        out->jsums[1] = jsums[1];
+    }
+    if (t < kCounters) out->counters[t] = counters[t];
+}
+
+}  // namespace
+
+void launch_commit(long long total, const int* status, const double* jsums, const double* tol_commit,
+                   const double* Unext, double* U, const long long* counters, IterCtl* ctl, cudaStream_t st) {
+    commit_kernel<<<grid_for(total, 256, 152 * 8), 256, 0, st>>>(total, status, jsums, tol_commit, Unext, U);
+    iter_ctl_kernel<<<1, 32, 0, st>>>(status, jsums, counters, ctl);
+}
+
 void launch_jumps(int ndof, int N, int NB, const double* U, const double* F, double* d, double* part,
                   double* sums, cudaStream_t st) {
     jumps_kernel<<<kJumpBlocks, 256, 0, st>>>(ndof, N, NB, U, F, d, part);
@@ -630,9 +664,19 @@ cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg) {
 }
 
 cudaError_t launch_cocg(const CocgArgs& a, bool fp32, const LaunchCfg& cfg, cudaStream_t st) {
-    void* args[] = {const_cast<CocgArgs*>(&a)};
-    const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
-    return cudaLaunchCooperativeKernel(fn, dim3(cfg.blocks), dim3(cfg.threads), args, cfg.smem, st);
+    // cudaLaunchKernelEx with the cooperative attribute: capturable in a graph
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(cfg.blocks);
+    lc.blockDim = dim3(cfg.threads);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (fp32) return cudaLaunchKernelEx(&lc, cocg_kernel<float>, a);
+    return cudaLaunchKernelEx(&lc, cocg_kernel<double>, a);
 }
 
 size_t cocg_smem_bytes(int H, int threads) { return cocg_smem(H, threads); }

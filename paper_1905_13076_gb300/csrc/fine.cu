@@ -624,6 +624,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
         for (size_t q = tid; q < 2 * len; q += blockDim.x) sv[q] = (T)0;   // p = s = 0
     }
     const int row0 = rs + rb;
+    const double tol_abs = a.tol_abs_dev ? *a.tol_abs_dev : a.tol_abs;
     // multigrid levels (precond = 2), copied to shared memory
     __shared__ AmgLevel s_amg[kAmgMaxLevels];
     const bool amg = a.amg != nullptr;
@@ -751,7 +752,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                     const double Rn = sqrt(rr);
                     const bool fin = isfinite(Rn);
                     // the adjoint's residual is linear: its tolerance is relative to ||b||
-                    const double tol = a.adjoint ? a.tol_rel * sqrt((double)s_sums[2 * NB + l]) : a.tol_abs;
+                    const double tol = a.adjoint ? a.tol_rel * sqrt((double)s_sums[2 * NB + l]) : tol_abs;
                     if (fin && (Rn <= tol || (nit > 0 && Rn <= kFloorMult * tol && Rn >= kStagnation * s_rprev[l]))) {
                         // converged, or stalled at the rounding floor just above the tolerance
                         s_newton[l] = 0;

@@ -81,6 +81,20 @@ struct pppc_handle {
     long long amg_units = 0;           // workspace per team, in units of the team's lanes
     void* amg_ws = nullptr;            // [amg_units * NB] of T
     std::vector<int> amg_rows;         // rows per level
+    // one PP-PC iteration as a captured CUDA graph (PP-PC method, no trace):
+    // run on gst; per-iteration inputs {Newton tolerance, commit threshold}
+    // from pinned ctl_in, the control block back into pinned ctl_out
+    cudaStream_t gst = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t gev = nullptr;         // end of a graph launch (timing fallback)
+    bool graph_dirty = true;
+    double* ctl_in = nullptr;          // pinned [2]
+    double* d_ctl_in = nullptr;        // device [2]
+    pppc::IterCtl* ctl_out = nullptr;  // pinned
+    pppc::IterCtl* d_ctl = nullptr;    // device
+    pppc::FineArgs* d_graph_args = nullptr;   // [kMaxTeams] the graph's own team arguments
+    int4* d_graph_map = nullptr;
+    int graph_kernels = 0;
     // the same hierarchy preconditioning the harmonic solves: two lanes per harmonic
     void *camg_ws = nullptr, *camg_J = nullptr, *camg_r = nullptr, *camg_z = nullptr;
     double* ext = nullptr;   // [N][n_nodes] staging for host states

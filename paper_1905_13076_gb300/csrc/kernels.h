@@ -83,6 +83,10 @@ void launch_ppic_step(int ndof, int N, int NB, int n, const double* F, const dou
 void launch_zero_pad_lanes(int ndof, int N, int NB, double* U, cudaStream_t st);
 void launch_idft_update(int ndof, int N, int NB, int H, bool fp32, const void* W, const double* F,
                         const double* tw, double* Unew, cudaStream_t st);
+// End of a captured PP-PC iteration: U = Unext unless *status != 0 or
+// rel_res <= *tol_commit, then the control block ctl (status, jump sums, counters).
+void launch_commit(long long total, const int* status, const double* jsums, const double* tol_commit,
+                   const double* Unext, double* U, const long long* counters, IterCtl* ctl, cudaStream_t st);
 
 // ---- layout conversion between [N][n_nodes] states and [ndof][NB] lanes ----
 void launch_state_to_lanes(int ndof, int n_nodes, int N, int NB, const int* node_of_dof,

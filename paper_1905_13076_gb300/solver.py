@@ -35,6 +35,36 @@ def _is_cuda_tensor(x) -> bool:
     return hasattr(x, "is_cuda") and bool(x.is_cuda)
 
 
+def _torch_allocator(stream):
+    """Device-memory callbacks (pppc_config.alloc / free_fn) that take the
+    handle's workspace from PyTorch's caching allocator on the handle's
+    stream, so it shows in torch.cuda.memory_allocated() and is reused by
+    PyTorch after the handle is destroyed.  None when PyTorch has no GPU."""
+    try:
+        import torch
+    except ImportError:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    dev = torch.cuda.current_device()
+    st = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+
+    def alloc(nbytes, ctx):
+        try:
+            s = torch.cuda.ExternalStream(st, device=dev) if st else torch.cuda.default_stream(dev)
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, s)
+        except Exception:
+            return None                      # the library reports PPPC_ERR_NOMEM
+
+    def free(ptr, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass                             # interpreter shutdown
+
+    return _lib.ALLOC_FN(alloc), _lib.FREE_FN(free)
+
+
 class PPPC:
     """Periodic Parareal with periodic coarse problem and multi-harmonic
     coarse solve on one GPU."""
@@ -44,7 +74,7 @@ class PPPC:
                  tol_lin: float = 1e-6, max_lin: int = 20000, tol_coarse: float = 1e-8,
                  max_coarse: int = 20000, eta0: float = 1e-2, predictor: int = 1, method: str = "pppc",
                  coarse_at: str = "U", newton_schedule: bool = False, precond: str = "jacobi",
-                 lane_team: int = 0, stream=None):
+                 lane_team: int = 0, stream=None, torch_memory: bool = True):
         self._lib = _lib.load()
         cfg = pppc_config()
         self._lib.pppc_config_default(ctypes.byref(cfg))
@@ -61,6 +91,11 @@ class PPPC:
         cfg.precond = {"jacobi": 0, "tridiag": 1, "amg": 2}[precond]
         cfg.lane_team = int(lane_team)
         cfg.stream = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+        # device memory from PyTorch's caching allocator (kept alive with the handle)
+        self._alloc = _torch_allocator(stream) if torch_memory else None
+        if self._alloc is not None:
+            cfg.alloc = ctypes.cast(self._alloc[0], ctypes.c_void_p)
+            cfg.free_fn = ctypes.cast(self._alloc[1], ctypes.c_void_p)
         self.cfg = cfg
         h = ctypes.c_void_p()
         check(self._lib.pppc_create(ctypes.byref(cfg), ctypes.byref(h)), None)

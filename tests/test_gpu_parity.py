@@ -534,3 +534,59 @@ def test_multigrid_harmonic_solves_match_oracle(precision):
             s.coarse_update(U, F)
             its[pc] = s.stats()["cocg_iters"]
     assert its["amg"] < 0.5 * its["jacobi"], its
+
+
+def test_workspace_comes_from_torch_caching_allocator():
+    """By default the handle's device workspace comes from PyTorch's caching
+    allocator (pppc_config.alloc / free_fn): torch.cuda.memory_allocated()
+    grows by about the workspace at set_mesh and drops back at close, and
+    results do not depend on where the memory came from."""
+    import torch
+
+    prob = workload("small")
+    U0 = physical_states(prob)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    s = gpu_solver(prob)
+    grown = torch.cuda.memory_allocated() - before
+    lanes = prob.N * (prob.mesh.dirichlet == 0).sum()
+    assert grown > 8 * lanes * 8                        # at least 8 FP64 lane vectors
+    F_torch = s.propagate_fine(U0)
+    s.close()
+    assert torch.cuda.memory_allocated() - before < 1024
+    with gpu_solver(prob, torch_memory=False) as s2:
+        assert torch.cuda.memory_allocated() - before < 1024
+        F_plain = s2.propagate_fine(U0)
+    assert np.array_equal(F_torch, F_plain)
+
+
+def test_each_iteration_is_one_captured_graph():
+    """PP-PC iterations run as one captured CUDA graph each (fine sweep,
+    jumps, Kbar, DFT, harmonic solves, inverse DFT + update, commit): the same
+    iterates, counts and fixed point as the host-sequenced path (taken here
+    because a Newton trace is on), one graph launch per iteration, and the
+    returned state is the first iterate that passed."""
+    prob = workload("small")
+    m = FEModel(prob)
+    runs = {}
+    for traced in (False, True):
+        with gpu_solver(prob, lane_team=-1) as s:
+            if traced:
+                s.set_trace(4)
+            s.set_state(np.zeros((prob.N, prob.mesh.n_nodes)))
+            iters, rr = s.solve_periodic(tol=1e-10, kmax=40)
+            st = s.stats()
+            U = s.get_state()
+            runs[traced] = (iters, rr, st, U)
+    (i0, r0, s0, U0), (i1, r1, s1, U1) = runs[False], runs[True]
+    assert i0 == i1 and r0 == pytest.approx(r1, rel=1e-9)
+    assert s0["graph_launches"] == i0 + 1 and s1["graph_launches"] == 0
+    # the graph also runs the (discarded) coarse solve of the last iteration
+    assert s0["pcg_iters"] == s1["pcg_iters"] and s0["cocg_iters"] >= s1["cocg_iters"]
+    assert rel(U0, U1) < 1e-12
+    ref = oracle_pppc(m, prob.N, prob.n_fine, prob.T, tol=1e-12, kmax=60)
+    assert rel(free(prob, U0), ref.U) < TOL64
+    # rel_res of the returned state is the one reported: no update after the last test
+    with gpu_solver(prob, lane_team=-1) as s:
+        s.set_state(U0)
+        assert s.iterate() == pytest.approx(r0, rel=1e-6)
