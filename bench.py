@@ -378,6 +378,12 @@ def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB:
 
 # ---- the large workload (headline) -------------------------------------------
 LARGE_LEVELS = 2   # fine implicit-Euler levels of every subinterval per timed step
+# DRAM bytes (read + written) per row and lane-iteration of the multigrid
+# fine team kernel, measured with ncu on a 250 x 500 mesh with the large
+# workload's N = 256 (working set above L2): 571.9 GB over 124 501 rows x
+# 33 920 lane-iterations.  The traffic grows in proportion to rows and
+# lane-iterations once the working set exceeds L2.
+TRAFFIC_PER_ROW_LANE_ITER = 135.4
 LARGE_DESC = ("coax large: nr=500 x ntheta=1000 (499001 DOFs), N=256, 200 fine steps, sigma=3e7, Brauer steel, "
               "40 A @ 50 Hz + 8 A @ 150 Hz")
 
@@ -481,10 +487,13 @@ def run_large(args, world, rank, local):
     alg_bytes = bpr["total"] * ndof * lane_rounds
     hbm_peak, peak_src = peaks()
     achieved = alg_bytes / fine_s / 1e9
+    launches = max(1, len(per))   # one fine launch per step
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "peak_source": peak_src, "kernel": "fine_batch_kernel<float>" if mixed else
-            "fine_batch_kernel<double>", "bytes_per_row_lane_iteration": bpr,
-            "pcg_lane_iterations": lane_rounds, "kernel_seconds": fine_s}
+            "traffic": TRAFFIC_PER_ROW_LANE_ITER * ndof * lane_rounds / launches if mixed else None,
+            "traffic_source": "ncu dram__bytes on the 250 x 500 mesh, N = 256, scaled per row and lane-iteration",
+            "algorithmic_bytes_per_launch": alg_bytes / launches,
+            "peak_source": peak_src, "kernel": "fine_batch_kernel<float>" if mixed else "fine_batch_kernel<double>",
+            "bytes_per_row_lane_iteration": bpr, "pcg_lane_iterations": lane_rounds, "kernel_seconds": fine_s}
 
     # parity at full size on sampled outputs: one fine level of two
     # subintervals (where the current is high) from rest, against the
