@@ -66,12 +66,28 @@ def test_adjoint_matches_oracle(name, precision, tol_p, tol_g):
         assert gg[i] == pytest.approx(g[i], rel=tol_g), (i, gg[i], g[i])
 
 
+def _tight_loss(prob, adjoint=False):
+    """The GPU's periodic loss solved to its rounding floor (rel_res <= 1e-13,
+    Newton 1e-13, PCG 1e-14), so that central differences at h = 1e-6 resolve
+    the gradient: with relative sensitivities theta dP/dtheta / P of 0.04 or
+    more, a loss error of 1e-14 P costs at most ~1e-7 of the difference."""
+    from paper_1905_13076_gb300 import from_problem
+
+    with from_problem(prob, tol_coarse=1e-13, tol_newton=1e-13, tol_lin=1e-14) as s:
+        iters, rr = s.solve_periodic(tol=1e-14, kmax=400, raise_on_fail=False)
+        assert rr <= 1e-13, rr
+        if adjoint:
+            return s.adjoint(REGION_SHEATH, tol=1e-12)
+        return s.adjoint(REGION_SHEATH, tol=1e-12)[0]
+
+
 def test_adjoint_gradient_matches_central_differences():
-    """dP/d(sigma, k1) of the GPU's own periodic solutions, h = 1e-5 relative."""
+    """dP/d(sigma, k1, k2, k3) of the GPU's own periodic solutions against
+    central differences with h = 1e-6 relative, within 1e-6."""
     prob = mid()
-    _, grad, _ = gpu_adjoint(prob)
-    h = 1e-5
-    for i, (attr, idx) in enumerate([("sigma", None), ("brauer", 0)]):
+    _, grad, _ = _tight_loss(prob, adjoint=True)
+    h = 1e-6
+    for i, (attr, idx) in enumerate([("sigma", None), ("brauer", 0), ("brauer", 1), ("brauer", 2)]):
         vals = []
         for f in (1 + h, 1 - h):
             p = copy.deepcopy(prob)
@@ -81,10 +97,10 @@ def test_adjoint_gradient_matches_central_differences():
             else:
                 arr[REGION_SHEATH, idx] *= f
             setattr(p, attr, arr)
-            vals.append(gpu_adjoint(p)[0])
+            vals.append(_tight_loss(p))
         theta = prob.sigma[REGION_SHEATH] if idx is None else prob.brauer[REGION_SHEATH, idx]
         fd = (vals[0] - vals[1]) / (2 * h * theta)
-        assert grad[i] == pytest.approx(fd, rel=1e-6), (attr, grad[i], fd)
+        assert grad[i] == pytest.approx(fd, rel=1e-6), (attr, idx, grad[i], fd)
 
 
 def test_autograd_function_returns_the_adjoint_gradient():
