@@ -216,7 +216,8 @@ def run_batched(args, local):
             mc = m.mesh_counts()
             bpr = pcg_bytes_per_row_lane(mixed, mc["special_rows"] / mc["ndof"], mc["nnz"] / mc["ndof"], p.N,
                                          tri=args.precond == "tridiag")
-            tot += bpr * mc["ndof"] * p.N * m.stats()["pcg_iters"]
+            # lane-vectors the PCG streamed (all lane teams of the member)
+            tot += bpr * mc["ndof"] * m.stats()["pcg_lane_rounds"]
         return tot
 
     batch = PPPCBatch(members, autotune=True)
@@ -239,6 +240,7 @@ def run_batched(args, local):
     value = units * args.steps / (sum(dev_ms) * 1e-3)
     achieved = fbytes / (fine_ms * 1e-3) / 1e9
     fteams, cteams = batch.teams()
+    blanes, bteams = batch.lanes()
     batch.close()
 
     # the same cables, one handle after another, one iteration each
@@ -278,7 +280,8 @@ def run_batched(args, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
                      "kernel": "fine_batch_kernel"},
-        "teams": {"fine": [int(x) for x in fteams], "cocg": [int(x) for x in cteams]},
+        "teams": {"fine": [int(x) for x in fteams], "cocg": [int(x) for x in cteams],
+                  "lanes_per_team": [int(x) for x in blanes], "lane_teams": [int(x) for x in bteams]},
         "retunes_timed": retunes, "gpu_launches": kernels, "clocks": clk.summary(),
         "time_to_steady_state": tts,
     }

@@ -418,11 +418,12 @@ pppc_status pppc_adjoint(pppc_handle* h, int32_t region, double tol, int32_t kma
  *   2. every member's coarse linearisation and right-hand side, one
  *      cooperative launch of all members' harmonic solves (again one team per
  *      member), and every member's inverse DFT + update.
- * Team sizes start from a cost model (rows x lanes x fine steps) and, with
- * autotune = 1, are re-balanced from the per-team times the kernels measure
- * (%globaltimer) whenever that shortens the predicted launch by more than
- * 10%; the graphs are captured again after every change of teams or of the
- * set of active members.
+ * Every member's fine sweep runs as lane teams (pppc_batch_get_lanes), each
+ * team a unit of the block split.  Block counts start from a cost model
+ * (rows x lanes x fine steps) and, with autotune = 1, are re-balanced from
+ * the per-team times the kernels measure (%globaltimer) whenever that
+ * shortens the predicted launch by more than 10%; the graphs are captured
+ * again after every change of teams or of the set of active members.
  *
  * Members are handles that already have a mesh, a source and a state, all
  * with the same precision, the PP-PC method, the same stream (cfg.stream)
@@ -471,6 +472,13 @@ pppc_status pppc_batch_get_stats(pppc_batch* b, pppc_batch_stats* out);
 /* Current team sizes (blocks) of each member in the fine and coarse
  * launches: fine_blocks[count], cocg_blocks[count] (each may be NULL). */
 pppc_status pppc_batch_get_teams(pppc_batch* b, int32_t* fine_blocks, int32_t* cocg_blocks);
+
+/* Lane split of each member's fine sweep in the batch: lanes_per_team[count]
+ * and teams[count] (each may be NULL).  A member's lanes run as teams of
+ * lanes_per_team lanes -- its size bucket's choice of the single-handle
+ * tuner (pppc_config.lane_team), widened while all members' teams outnumber
+ * the SMs -- and every team is a unit of the batch's block split. */
+pppc_status pppc_batch_get_lanes(pppc_batch* b, int32_t* lanes_per_team, int32_t* teams);
 
 /* Last error on b, or of the last failed pppc_batch_create when b is NULL. */
 const char* pppc_batch_last_error(pppc_batch* b);

@@ -120,6 +120,7 @@ SIGNATURES = {
     "pppc_batch_solve_periodic": (c_int32, [c_void_p, c_double, c_int32, _IPTR, _DPTR]),
     "pppc_batch_get_stats": (c_int32, [c_void_p, POINTER(pppc_batch_stats)]),
     "pppc_batch_get_teams": (c_int32, [c_void_p, _IPTR, _IPTR]),
+    "pppc_batch_get_lanes": (c_int32, [c_void_p, _IPTR, _IPTR]),
     "pppc_batch_last_error": (c_char_p, [c_void_p]),
     "pppc_batch_plan": (c_int32, [_DPTR, _IPTR, _IPTR, c_int32, c_int32, _IPTR, _DPTR]),
 }

@@ -188,7 +188,9 @@ std::vector<int> team_candidates(const pppc_handle* h) {
     return c;
 }
 
-pppc_status row_tables_for(pppc_handle* h, int blocks, const pppc_row_tables** out) {
+}  // namespace
+
+pppc_status pppc::detail::row_tables_for(pppc_handle* h, int blocks, const pppc_row_tables** out) {
     auto it = h->row_tables.find(blocks);
     if (it == h->row_tables.end()) {
         std::vector<int> rs, ls, lr;
@@ -202,6 +204,8 @@ pppc_status row_tables_for(pppc_handle* h, int blocks, const pppc_row_tables** o
     *out = &it->second;
     return PPPC_OK;
 }
+
+namespace {
 
 // Teams of `lanes` lanes, the SMs split as evenly as the team count allows.
 pppc_status make_plan(pppc_handle* h, int lanes, pppc_fine_plan* p) {
@@ -222,48 +226,17 @@ pppc_status make_plan(pppc_handle* h, int lanes, pppc_fine_plan* p) {
     return PPPC_OK;
 }
 
-// The sweep `base` (one team over all lanes) as the teams of plan p:
-// per-team arguments with the team's lanes, its regions of the PCG vectors
-// and partial sums, its barrier and its row partition, and the block map.
+// The sweep `base` (one team over all lanes) as the teams of plan p, and
+// the block -> (team, block in team, team size) map.
 void team_tables(pppc_handle* h, const pppc_fine_plan& p, const FineArgs& base, std::vector<FineArgs>& args,
                  std::vector<int4>& map) {
-    const size_t ts = h->fp32 ? sizeof(float) : sizeof(double);
-    const size_t ndof = h->hm.ndof;
-    auto at = [&](void* b, size_t elems) -> void* { return b ? static_cast<char*>(b) + elems * ts : nullptr; };
     args.assign(p.teams, FineArgs{});
     map.assign(h->sms, make_int4(-1, 0, 0, 0));
-    const size_t budget = h->smem_optin - h->fine_static_smem - 1024;
     size_t part_off = 0;
     int first = 0;
     for (int t = 0; t < p.teams; ++t) {
-        FineArgs a = base;
         const int nb = p.blocks[t];
-        const pppc_row_tables& rt = h->row_tables.at(nb);
-        a.NB = p.lanes;
-        a.lane0 = t * p.lanes;
-        a.ld = h->NB;
-        a.n_teams = p.teams;
-        const size_t v = (size_t)t * ndof * p.lanes;
-        a.r = at(h->r, v);
-        a.z = at(h->z, v);
-        a.w = at(h->w, v);
-        a.p = at(h->p, v);
-        a.s = at(h->s, v);
-        a.x = at(h->x, v);
-        a.dx = at(h->dx, v);
-        a.tri_m = at(h->tri_m, v);
-        a.tri_ie = at(h->tri_ie, v);
-        a.J = at(h->J, (size_t)t * h->hm.n_slots * p.lanes);
-        a.invd_sp = at(h->invd, (size_t)t * h->hm.n_sp * p.lanes);
-        a.part = at(h->part, part_off);
-        part_off += 2 * (size_t)nb * 3 * p.lanes;   // two buffers of 3 sums per lane and block
-        a.amg_ws = at(h->amg_ws, (size_t)t * h->amg_units * p.lanes);
-        a.bar = h->bar + t;
-        a.row_start = rt.rs;
-        a.long_start = rt.ls;
-        a.long_rows = rt.lr;
-        choose_vec_rows(h->fp32, p.lanes, rt.rows_max, budget, &a.vec_rows, &a.vec_w);
-        args[t] = a;
+        args[t] = team_args(h, p.lanes, t, p.teams, nb, base, &part_off);
         for (int k = 0; k < nb; ++k) map[first + k] = make_int4(t, k, nb, 0);
         first += nb;
     }
@@ -333,6 +306,16 @@ pppc_status choose_plan(pppc_handle* h, const double* Uin, double* Fout) {
     }
     return PPPC_OK;
 }
+
+}  // namespace
+
+pppc_status pppc::detail::sweep_lanes(pppc_handle* h, int* lanes) {
+    TRY(choose_plan(h, h->U, h->F));
+    *lanes = h->plan.lanes > 0 ? h->plan.lanes : h->NB;
+    return PPPC_OK;
+}
+
+namespace {
 
 // ---- stages of one iteration ----------------------------------------------
 
@@ -504,6 +487,46 @@ double pppc::detail::fine_cost_estimate(const pppc_handle* h) {
         c += 2.0 + nz * (hm.row_slot[i] >= 0 ? 2.0 : 1.0);
     }
     return c * h->NB * h->cfg.n_fine;
+}
+
+FineArgs pppc::detail::team_args(pppc_handle* h, int lanes, int t, int teams, int nb, const FineArgs& base,
+                                 size_t* part_off) {
+    const size_t ts = h->fp32 ? sizeof(float) : sizeof(double);
+    const size_t ndof = h->hm.ndof;
+    auto at = [&](void* b, size_t elems) -> void* { return b ? static_cast<char*>(b) + elems * ts : nullptr; };
+    const pppc_row_tables& rt = h->row_tables.at(nb);
+    FineArgs a = base;
+    a.NB = lanes;
+    a.lane0 = t * lanes;
+    a.ld = h->NB;
+    a.n_teams = teams;
+    const size_t v = (size_t)t * ndof * lanes;
+    a.r = at(h->r, v);
+    a.z = at(h->z, v);
+    a.w = at(h->w, v);
+    a.p = at(h->p, v);
+    a.s = at(h->s, v);
+    a.x = at(h->x, v);
+    a.dx = at(h->dx, v);
+    a.tri_m = at(h->tri_m, v);
+    a.tri_ie = at(h->tri_ie, v);
+    a.J = at(h->J, (size_t)t * h->hm.n_slots * lanes);
+    a.invd_sp = at(h->invd, (size_t)t * h->hm.n_sp * lanes);
+    a.part = at(h->part, *part_off);
+    *part_off += 2 * (size_t)nb * 3 * lanes;   // two buffers of 3 sums per lane and block
+    a.amg_ws = at(h->amg_ws, (size_t)t * h->amg_units * lanes);
+    a.bar = h->bar + t;
+    a.row_start = rt.rs;
+    a.long_start = rt.ls;
+    a.long_rows = rt.lr;
+    const size_t budget = h->smem_optin - h->fine_static_smem - 1024;
+    choose_vec_rows(h->fp32, lanes, rt.rows_max, budget, &a.vec_rows, &a.vec_w);
+    if (t > 0) {   // the Newton trace records one team's lanes
+        a.trace = nullptr;
+        a.trace_cap = 0;
+        a.trace_len = nullptr;
+    }
+    return a;
 }
 
 void pppc::detail::choose_vec_rows(bool fp32, int NB, int rows_max, size_t budget, int* vec_rows, int* vec_w) {

@@ -38,6 +38,8 @@ thread_local std::string g_batch_create_error;
 
 // Retune only when the re-split is predicted to shorten the launch by this.
 constexpr double kRetuneGain = 0.9;
+// A member's lane teams each expect at least this many blocks of the batch.
+constexpr int kMinTeamBlocks = 8;
 
 // Where member c's control words live, and what is gathered from them.
 struct CtlSrc {
@@ -88,10 +90,15 @@ struct pppc_batch {
     CtlSrc* d_src = nullptr;
     CtlOut* d_ctl = nullptr;
     CtlOut* h_ctl = nullptr;          // pinned host copy
-    std::vector<int*> d_rs, d_ls, d_lr;
+    // fine launch: every member's lane teams are units of their own
+    std::vector<int> lanes, teams, unit_first;   // per member
+    std::vector<int> unit_member;                // per unit
+    int units = 0;
+    long long* d_unit_ns = nullptr;   // [units][2] %globaltimer at a unit's start and end
+    long long* h_unit_ns = nullptr;   // pinned copy
     // host state
-    std::vector<int> fblocks, cblocks;
-    std::vector<double> fcost, ccost;  // per member: time x blocks (model units until measured)
+    std::vector<int> fblocks, cblocks;   // fblocks per unit, cblocks per member
+    std::vector<double> fcost, ccost;    // per unit / per member: time x blocks (model units until measured)
     std::vector<char> active;
     size_t fine_smem_launch = 0, cocg_smem_launch = 0;
     cudaGraphExec_t gfine = nullptr, gcoarse = nullptr;
@@ -172,8 +179,8 @@ double split_blocks(const std::vector<double>& cost, const std::vector<char>& ac
     return mk;
 }
 
-int fine_cap(const pppc_handle* h) {
-    const int V = h->fp32 ? 4 : 2, RB = 1024 / (h->NB / V);
+int fine_cap(const pppc_handle* h, int lanes) {
+    const int V = h->fp32 ? 4 : 2, RB = 1024 / (lanes / V);
     return std::max(1, h->hm.ndof / (2 * RB));
 }
 
@@ -229,46 +236,47 @@ pppc_status end_capture(pppc_batch* b, cudaGraphExec_t* exec) {
 pppc_status rebuild(pppc_batch* b) {
     BCK(cudaStreamSynchronize(b->st));
     destroy_graphs(b);
-    const int n = b->count;
-    std::vector<int> fcap(n), ccap(n);
-    for (int c = 0; c < n; ++c) {
-        fcap[c] = fine_cap(b->m[c]);
-        ccap[c] = cocg_cap(b->m[c]);
+    const int n = b->count, nu = b->units;
+    std::vector<int> fcap(nu), ccap(n);
+    std::vector<char> uactive(nu);
+    for (int u = 0; u < nu; ++u) {
+        const int c = b->unit_member[u];
+        fcap[u] = fine_cap(b->m[c], b->lanes[c]);
+        uactive[u] = b->active[c];
     }
-    split_blocks(b->fcost, b->active, fcap, b->sms, b->fblocks);
+    for (int c = 0; c < n; ++c) ccap[c] = cocg_cap(b->m[c]);
+    split_blocks(b->fcost, uactive, fcap, b->sms, b->fblocks);
     split_blocks(b->ccost, b->active, ccap, b->sms, b->cblocks);
 
-    // fine: row partition per member, shared-memory vectors where they fit
-    const size_t budget = b->smem_optin - b->fine_static - 1024;
-    std::vector<FineArgs> fa(n);
+    // fine: one unit per lane team of every active member, each with the row
+    // partition of its block count and shared-memory vectors where they fit
+    std::vector<FineArgs> fa(nu);
     std::vector<CocgArgs> ca(n);
     b->fine_smem_launch = 0;
     b->cocg_smem_launch = 0;
     for (int c = 0; c < n; ++c) {
         pppc_handle* h = b->m[c];
-        fa[c] = fine_args(h, h->F);
         ca[c] = cocg_args(h);
-        fa[c].team_ns = b->d_team_ns + 4 * (size_t)c;
         ca[c].team_ns = b->d_team_ns + 4 * (size_t)c + 2;
-        if (!b->active[c]) continue;
-        std::vector<int> rs, ls, lr;
-        int rows_max = 0;
-        partition_rows(h->hm, b->fblocks[c], rs, ls, lr, &rows_max);
-        BCK(cudaMemcpyAsync(b->d_rs[c], rs.data(), rs.size() * sizeof(int), cudaMemcpyHostToDevice, b->st));
-        BCK(cudaMemcpyAsync(b->d_ls[c], ls.data(), ls.size() * sizeof(int), cudaMemcpyHostToDevice, b->st));
-        if (!lr.empty())
-            BCK(cudaMemcpyAsync(b->d_lr[c], lr.data(), lr.size() * sizeof(int), cudaMemcpyHostToDevice, b->st));
-        int vr = 0, vw = 0;
-        choose_vec_rows(b->fp32, h->NB, rows_max, budget, &vr, &vw);
-        fa[c].row_start = b->d_rs[c];
-        fa[c].long_start = b->d_ls[c];
-        fa[c].long_rows = b->d_lr[c];
-        fa[c].vec_rows = vr;
-        fa[c].vec_w = vw;
-        b->fine_smem_launch = std::max(b->fine_smem_launch, fine_smem(b->fp32, h->NB, 1024, vr, vw ? 4 : 3));
-        b->cocg_smem_launch = std::max(b->cocg_smem_launch, cocg_smem_bytes(h->H, 512));
+        const FineArgs base = fine_args(h, h->F);
+        size_t part_off = 0;
+        for (int t = 0; t < b->teams[c]; ++t) {
+            const int u = b->unit_first[c] + t;
+            if (!b->active[c]) {
+                fa[u] = base;
+                continue;
+            }
+            const pppc_row_tables* rt = nullptr;
+            const pppc_status st = row_tables_for(h, b->fblocks[u], &rt);
+            if (st != PPPC_OK) return bfail(b, st, "member " + std::to_string(c) + ": " + h->err);
+            fa[u] = team_args(h, b->lanes[c], t, b->teams[c], b->fblocks[u], base, &part_off);
+            fa[u].team_ns = b->d_unit_ns + 2 * (size_t)u;
+            b->fine_smem_launch = std::max(b->fine_smem_launch,
+                                           fine_smem(b->fp32, b->lanes[c], 1024, fa[u].vec_rows, fa[u].vec_w ? 4 : 3));
+        }
+        if (b->active[c]) b->cocg_smem_launch = std::max(b->cocg_smem_launch, cocg_smem_bytes(h->H, 512));
     }
-    BCK(cudaMemcpyAsync(b->d_fargs, fa.data(), n * sizeof(FineArgs), cudaMemcpyHostToDevice, b->st));
+    BCK(cudaMemcpyAsync(b->d_fargs, fa.data(), nu * sizeof(FineArgs), cudaMemcpyHostToDevice, b->st));
     BCK(cudaMemcpyAsync(b->d_cargs, ca.data(), n * sizeof(CocgArgs), cudaMemcpyHostToDevice, b->st));
     std::vector<int4> fmap, cmap;
     team_map(b->sms, b->fblocks, fmap);
@@ -282,13 +290,14 @@ pppc_status rebuild(pppc_batch* b) {
     b->fine_kernels = 0;
     BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
     CAP(cudaMemsetAsync(b->d_team_ns, 0, 4 * (size_t)n * sizeof(long long), b->st));
+    CAP(cudaMemsetAsync(b->d_unit_ns, 0, 2 * (size_t)nu * sizeof(long long), b->st));
     for (int c = 0; c < n; ++c) {
         if (!b->active[c]) continue;
         pppc_handle* h = b->m[c];
         CAP(cudaMemcpyAsync(h->F, h->U, (size_t)h->hm.ndof * h->NB * sizeof(double), cudaMemcpyDeviceToDevice,
                             b->st));
         CAP(cudaMemsetAsync(h->status, 0, sizeof(int), b->st));
-        CAP(cudaMemsetAsync(h->bar, 0, sizeof(GridBarrier), b->st));
+        CAP(cudaMemsetAsync(h->bar, 0, kMaxTeams * sizeof(GridBarrier), b->st));
         CAP(reset_team_ctl(h, b->st));
     }
     CAP(launch_fine_batch(b->d_fargs, b->d_fmap, b->fp32, b->sms, b->fine_smem_launch, b->st));
@@ -303,6 +312,8 @@ pppc_status rebuild(pppc_batch* b) {
     b->fine_kernels += 1;
     CAP(cudaGetLastError());
     CAP(cudaMemcpyAsync(b->h_ctl, b->d_ctl, n * sizeof(CtlOut), cudaMemcpyDeviceToHost, b->st));
+    CAP(cudaMemcpyAsync(b->h_unit_ns, b->d_unit_ns, 2 * (size_t)nu * sizeof(long long), cudaMemcpyDeviceToHost,
+                        b->st));
     BTRY(end_capture(b, &b->gfine));
 
     // ---- coarse graph
@@ -378,20 +389,27 @@ void retune(pppc_batch* b, bool fine) {
     if (!b->autotune) return;
     std::vector<double>& cost = fine ? b->fcost : b->ccost;
     const std::vector<int>& blocks = fine ? b->fblocks : b->cblocks;
-    const int q = fine ? 0 : 2;
+    const int items = fine ? b->units : b->count;
     double measured = 0.0;
     std::vector<double> next = cost;
-    for (int c = 0; c < b->count; ++c) {
-        if (!b->active[c] || blocks[c] < 1) continue;
-        const long long t0 = b->h_ctl[c].t[q], t1 = b->h_ctl[c].t[q + 1];
+    std::vector<char> act(items);
+    for (int i = 0; i < items; ++i) {
+        const int c = fine ? b->unit_member[i] : i;
+        act[i] = b->active[c];
+        if (!act[i] || blocks[i] < 1) continue;
+        const long long t0 = fine ? b->h_unit_ns[2 * i] : b->h_ctl[c].t[2];
+        const long long t1 = fine ? b->h_unit_ns[2 * i + 1] : b->h_ctl[c].t[3];
         if (t0 <= 0 || t1 < t0) return;   // no complete record: keep the teams
         const double t = (double)(t1 - t0);
         measured = std::max(measured, t);
-        next[c] = t * blocks[c];
+        next[i] = t * blocks[i];
     }
-    std::vector<int> cap(b->count), trial;
-    for (int c = 0; c < b->count; ++c) cap[c] = fine ? fine_cap(b->m[c]) : cocg_cap(b->m[c]);
-    const double predicted = split_blocks(next, b->active, cap, b->sms, trial);
+    std::vector<int> cap(items), trial;
+    for (int i = 0; i < items; ++i) {
+        const int c = fine ? b->unit_member[i] : i;
+        cap[i] = fine ? fine_cap(b->m[c], b->lanes[c]) : cocg_cap(b->m[c]);
+    }
+    const double predicted = split_blocks(next, act, cap, b->sms, trial);
     cost = next;
     if (predicted < kRetuneGain * measured && trial != blocks) {
         b->dirty = true;
@@ -476,6 +494,7 @@ void pppc_batch_destroy(pppc_batch* b) {
             cudaFree(p);
     }
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->h_unit_ns) cudaFreeHost(b->h_unit_ns);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
     delete b;
@@ -551,25 +570,72 @@ pppc_status pppc_batch_create(pppc_handle* const* members, int32_t count, int32_
     auto take = [&](pppc_status r) {
         if (s == PPPC_OK) s = r;
     };
-    take(balloc(b, &b->d_fargs, count));
+    // every member's lane split: its size bucket's tuned choice (the same
+    // tuner as a single handle, timed on the member's state if its bucket has
+    // none yet); splits are widened while the teams outnumber the SMs
+    b->lanes.assign(count, 0);
+    b->teams.assign(count, 1);
+    for (int c = 0; c < count; ++c) {
+        pppc_handle* h = members[c];
+        int lanes = 0;
+        const pppc_status ls = sweep_lanes(h, &lanes);
+        if (ls != PPPC_OK) {
+            b->err = "member " + std::to_string(c) + ": " + h->err;
+            return undo(ls);
+        }
+        b->lanes[c] = lanes;
+        b->teams[c] = h->NB / lanes;
+    }
+    // inside a batch a member gets only its share of the SMs (cost model):
+    // its split is widened until every team can expect kMinTeamBlocks blocks
+    {
+        double sum = 0.0;
+        for (int c = 0; c < count; ++c) sum += fine_cost_estimate(members[c]);
+        for (int c = 0; c < count; ++c) {
+            const double share = sms * fine_cost_estimate(members[c]) / sum;
+            while (b->teams[c] > 1 && b->teams[c] * kMinTeamBlocks > share) {
+                b->lanes[c] *= 2;
+                b->teams[c] = members[c]->NB / b->lanes[c];
+            }
+        }
+    }
+    for (;;) {
+        int total = 0, widest = -1;
+        for (int c = 0; c < count; ++c) {
+            total += b->teams[c];
+            if (b->teams[c] > 1 && (widest < 0 || b->teams[c] > b->teams[widest])) widest = c;
+        }
+        if (total <= sms) break;
+        if (widest < 0) {
+            b->err = "more lane teams than SMs";
+            return undo(PPPC_ERR_UNSUPPORTED);
+        }
+        b->lanes[widest] *= 2;
+        b->teams[widest] = members[widest]->NB / b->lanes[widest];
+    }
+    b->unit_first.assign(count, 0);
+    b->unit_member.clear();
+    for (int c = 0; c < count; ++c) {
+        b->unit_first[c] = (int)b->unit_member.size();
+        for (int t = 0; t < b->teams[c]; ++t) b->unit_member.push_back(c);
+    }
+    b->units = (int)b->unit_member.size();
+    take(balloc(b, &b->d_fargs, b->units));
     take(balloc(b, &b->d_cargs, count));
     take(balloc(b, &b->d_fmap, sms));
     take(balloc(b, &b->d_cmap, sms));
     take(balloc(b, &b->d_team_ns, 4 * (size_t)count));
+    take(balloc(b, &b->d_unit_ns, 2 * (size_t)b->units));
     take(balloc(b, &b->d_src, count));
     take(balloc(b, &b->d_ctl, count));
-    b->d_rs.assign(count, nullptr);
-    b->d_ls.assign(count, nullptr);
-    b->d_lr.assign(count, nullptr);
-    for (int c = 0; c < count && s == PPPC_OK; ++c) {
-        const HostMesh& hm = members[c]->hm;
-        int nlong = 0;
-        for (int i = 0; i < hm.ndof; ++i) nlong += (hm.rowptr[i + 1] - hm.rowptr[i]) > 32;
-        take(balloc(b, &b->d_rs[c], sms + 1));
-        take(balloc(b, &b->d_ls[c], sms + 1));
-        take(balloc(b, &b->d_lr[c], std::max(nlong, 1)));
-    }
     if (s != PPPC_OK) return undo(s);
+    if (cudaMallocHost(&b->h_unit_ns, 2 * (size_t)b->units * sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
+        b->h_unit_ns = nullptr;
+        b->err = "pinned host allocation failed";
+        return undo(PPPC_ERR_NOMEM);
+    }
+    std::memset(b->h_unit_ns, 0, 2 * (size_t)b->units * sizeof(long long));
     if (cudaMallocHost(&b->h_ctl, count * sizeof(CtlOut)) != cudaSuccess) {
         cudaGetLastError();
         b->h_ctl = nullptr;
@@ -595,13 +661,15 @@ pppc_status pppc_batch_create(pppc_handle* const* members, int32_t count, int32_
         b->err = "batch table upload failed";
         return undo(PPPC_ERR_CUDA);
     }
-    b->fcost.resize(count);
+    b->fcost.resize(b->units);
     b->ccost.resize(count);
+    for (int u = 0; u < b->units; ++u) {
+        const int c = b->unit_member[u];
+        b->fcost[u] = fine_cost_estimate(members[c]) / b->teams[c];
+    }
     for (int c = 0; c < count; ++c) {
-        const pppc_handle* h = members[c];
-        b->fcost[c] = fine_cost_estimate(h);
         // COCG: one complex row per harmonic, a few hundred iterations either way
-        b->ccost[c] = (double)h->hm.ndof * h->H;
+        b->ccost[c] = (double)members[c]->hm.ndof * members[c]->H;
     }
     b->active.assign(count, 1);
     *out = b;
@@ -680,8 +748,22 @@ pppc_status pppc_batch_plan(const double* cost, const int32_t* cap, const int32_
 pppc_status pppc_batch_get_teams(pppc_batch* b, int32_t* fine_blocks, int32_t* cocg_blocks) {
     if (!b) return PPPC_ERR_INVALID_ARG;
     for (int c = 0; c < b->count; ++c) {
-        if (fine_blocks) fine_blocks[c] = c < (int)b->fblocks.size() ? b->fblocks[c] : 0;
+        int fb = 0;
+        for (int t = 0; t < b->teams[c]; ++t) {
+            const int u = b->unit_first[c] + t;
+            fb += u < (int)b->fblocks.size() ? b->fblocks[u] : 0;
+        }
+        if (fine_blocks) fine_blocks[c] = fb;
         if (cocg_blocks) cocg_blocks[c] = c < (int)b->cblocks.size() ? b->cblocks[c] : 0;
+    }
+    return PPPC_OK;
+}
+
+pppc_status pppc_batch_get_lanes(pppc_batch* b, int32_t* lanes_per_team, int32_t* teams) {
+    if (!b) return PPPC_ERR_INVALID_ARG;
+    for (int c = 0; c < b->count; ++c) {
+        if (lanes_per_team) lanes_per_team[c] = b->lanes[c];
+        if (teams) teams[c] = b->teams[c];
     }
     return PPPC_OK;
 }

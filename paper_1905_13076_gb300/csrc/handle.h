@@ -135,6 +135,16 @@ pppc_status device_status(pppc_handle* h, const char* where);
 FineArgs fine_args(pppc_handle* h, double* Fout);
 // Zero h's per-sweep team control words (sweep maxima, teams done) on stream st.
 cudaError_t reset_team_ctl(pppc_handle* h, cudaStream_t st);
+// Arguments of lane team t (lanes lanes from lane t * lanes, one of `teams`)
+// of the sweep `base` on nb blocks: its regions of the PCG vectors, partial
+// sums (at *part_off, advanced) and multigrid workspace, its barrier and the
+// row partition for nb blocks (row_tables_for must have built it).
+FineArgs team_args(pppc_handle* h, int lanes, int t, int teams, int nb, const FineArgs& base, size_t* part_off);
+// The row partition of h's fine sweep over nb blocks, built on first use.
+pppc_status row_tables_for(pppc_handle* h, int nb, const pppc_row_tables** out);
+// Lanes per team of h's fine sweep: the handle's plan, chosen (by the tuner
+// with pppc_config.lane_team = 0, from the handle's state) if not yet.
+pppc_status sweep_lanes(pppc_handle* h, int* lanes);
 // Arguments of h's batched harmonic solve (Eq. 13).
 CocgArgs cocg_args(pppc_handle* h);
 // Stages of one iteration on h's stream: mesh and source present; control

@@ -352,6 +352,14 @@ class PPPCBatch:
                                                    c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
         return f, c
 
+    def lanes(self):
+        """Per member: (lanes per team, teams) of its fine sweep in the batch."""
+        lp = np.zeros(len(self.members), dtype=np.int32)
+        tm = np.zeros(len(self.members), dtype=np.int32)
+        self._check(self._lib.pppc_batch_get_lanes(self._b, lp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                   tm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return lp, tm
+
     def stats(self) -> dict:
         s = _lib.pppc_batch_stats()
         self._check(self._lib.pppc_batch_get_stats(self._b, ctypes.byref(s)))
