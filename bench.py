@@ -6,9 +6,9 @@ Default: the large coax workload, 499 001 DOFs, N = 256 subintervals of 200
 implicit-Euler steps, Brauer steel sheath with sigma = 3e7 S/m, 40 A at
 50 Hz + 8 A at 150 Hz, mixed precision, multigrid-preconditioned fine PCG and
 harmonic COCG.  One PP-PC iteration there takes minutes, so a "step" is a
-fixed slice of it: 2 fine levels of all 256 subintervals (continuing the
+fixed slice of it: 4 fine levels of all 256 subintervals (continuing the
 first iteration's sweep from U = 0) plus one complete coarse update.
-value = fine DOF-steps per second (N * 2 * ndof per step) over the timed
+value = fine DOF-steps per second (N * 4 * ndof per step) over the timed
 steps, device time from CUDA events on the library's stream; every state is
 larger than L2.  Also reported: one whole PP-PC iteration timed once, the
 time to periodic steady state at rel_res 1e-8 extrapolated from it and from
@@ -380,7 +380,7 @@ def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB:
 
 
 # ---- the large workload (headline) -------------------------------------------
-LARGE_LEVELS = 2   # fine implicit-Euler levels of every subinterval per timed step
+LARGE_LEVELS = 4   # fine implicit-Euler levels of every subinterval per timed step
 # DRAM bytes (read + written) per row and lane-iteration of the multigrid
 # fine team kernel, measured with ncu on a 250 x 500 mesh with the large
 # workload's N = 256 (working set above L2): 571.9 GB over 124 501 rows x

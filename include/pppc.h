@@ -136,8 +136,9 @@ typedef struct pppc_config {
                              2 one V-cycle of smoothed-aggregation algebraic multigrid: the
                              aggregates and prolongators are built once by pppc_set_mesh from
                              the Newton matrix at zero field, each subinterval's coarse matrices
-                             are the Galerkin products of its own Jacobian (rebuilt every Newton
-                             iteration), with l1-Jacobi smoothing on every level, so the
+                             are the Galerkin products of its own Jacobian (rebuilt at the first
+                             Newton iteration of every fine step), with l1-Jacobi smoothing on
+                             every level, so the
                              preconditioner stays symmetric positive definite for every lane
                              and its iteration count hardly grows with the mesh; a mesh too
                              small to coarsen falls back to Jacobi */

@@ -714,9 +714,12 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
             else
                 residual_rows<T, V>(a, m, row0, re, RB, l0, s_I, accR, accz, xB, vo, l1f);
             if (amg) {
-                // every lane's coarse matrices from its new Jacobian, then z = B r
+                // every lane's coarse matrices from its Jacobian at the step's
+                // first Newton iteration (the later iterations of the step keep
+                // them: Galerkin products of an SPD Jacobian stay SPD, and the
+                // fine level smooths with the current Jacobian), then z = B r
                 if (!grid_sync(a.bar, a.status, bid, nblk)) return;
-                if (!amg_coarse_values<T, V>(actx, s_amg, bid, nblk)) return;
+                if (nit == 0 && !amg_coarse_values<T, V>(actx, s_amg, bid, nblk)) return;
                 if (!amg_vcycle<T, V>(actx, m, s_amg, KlinT, J, r, z, bid, nblk, re, row0, RB, rb, l0, G, s_red, s_tmp))
                     return;
             } else if (a.tri > 0) {
