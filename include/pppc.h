@@ -114,7 +114,8 @@ typedef struct pppc_config {
     int32_t max_newton;   /* Newton iteration cap per fine step */
     double tol_lin;       /* smallest PCG forcing term (relative residual of one solve) */
     int32_t max_lin;      /* PCG iteration cap per Newton iteration */
-    double tol_coarse;    /* COCG: ||r_p|| <= tol_coarse * ||b_p|| per harmonic */
+    double tol_coarse;    /* COCG stops harmonic p at ||r_p||^2 <= tol_coarse^2 *
+                             max(||b_p||^2, sum_q ||b_q||^2 / (N/2+1)) */
     int32_t max_coarse;   /* COCG iteration cap */
     void* stream;         /* cudaStream_t; NULL = legacy default stream */
     pppc_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc) */
@@ -281,8 +282,11 @@ pppc_status pppc_solve_periodic(pppc_handle* h, double tol, int32_t kmax, int32_
  * first, and col only once rowptr has passed, so a bad pattern returns
  * PPPC_ERR_INVALID_ARG without any out-of-range access.  b and x are
  * complex, interleaved (re, im), laid out [n][N/2+1].  All pointers are
- * device memory owned by the caller; the call stops when
- * ||r_p|| <= tol ||b_p|| for every p or after max_it iterations, writes the
+ * device memory owned by the caller; the call stops when every harmonic's
+ * ||r_p||^2 <= tol^2 * max(||b_p||^2, sum_q ||b_q||^2 / (N/2+1)) (its own
+ * relative tol, or tol times the average right-hand side where its own is
+ * smaller; the sum over p of ||r_p||^2 stays within 2 tol^2 times that of
+ * ||b_p||^2) or after max_it iterations, writes the
  * iterations done to *iters_out (may be NULL) and synchronises `stream`
  * (a cudaStream_t, NULL = legacy default stream) before returning.
  *

@@ -13,8 +13,9 @@ namespace pppc {
 
 // What a V-cycle needs from its caller: the team's lanes (row stride of all
 // its vectors), levels, coarsest sweeps, workspace, the fine level's
-// per-lane special-row values, the team barrier and status word, and the
-// long rows of each block's own fine rows.
+// per-lane special-row values, the team barrier and status word, the long
+// rows of each block's own fine rows, and the block's rows of every coarse
+// level.
 struct AmgCtx {
     int NB, levels, sweeps;
     void* ws;
@@ -23,6 +24,7 @@ struct AmgCtx {
     int* status;
     const int* long_start;
     const int* long_rows;
+    const int2* rng;   // [levels] this block's rows [x, y) of every coarse level (amg_block_ranges)
 };
 
 // ---- multigrid preconditioner (precond = 2) -------------------------------
@@ -38,7 +40,9 @@ struct AmgCtx {
 // acc += sum_{k in [kb, ke)} w[k] x[idx[k]] for this thread's V lanes, with
 // shared scalar weights; four gathers are issued before any is consumed
 // (the rows of the coarse levels and of R are long, and a gather that waits
-// for its index and then its vector would serialise on memory latency).
+// for its index and then its vector would serialise on memory latency), and
+// the last 1-3 entries form one more such group (a 7-entry fine row takes
+// two rounds of loads, not four); its unused places reload entry k.
 template <typename T, int V>
 __device__ __forceinline__ void gather_shared(T (&acc)[V], int kb, int ke, const int* __restrict__ idx,
                                               const T* __restrict__ w, const T* x, int NB, int l0) {
@@ -53,11 +57,21 @@ __device__ __forceinline__ void gather_shared(T (&acc)[V], int kb, int ke, const
 #pragma unroll
         for (int h = 0; h < V; ++h) acc[h] += (w0 * x0.v[h] + w1 * x1.v[h]) + (w2 * x2.v[h] + w3 * x3.v[h]);
     }
-    for (; k < ke; ++k) {
-        const T wk = w[k];
-        const Lanes<T, V> xk = ldv<T, V>(x + (size_t)idx[k] * NB + l0);
+    if (k < ke) {
+        const int nr = ke - k;
+        const int k1 = nr > 1 ? k + 1 : k, k2 = nr > 2 ? k + 2 : k;
+        const int i0 = idx[k], i1 = idx[k1], i2 = idx[k2];
+        const T w0 = w[k], w1 = w[k1], w2 = w[k2];
+        const Lanes<T, V> x0 = ldv<T, V>(x + (size_t)i0 * NB + l0);
+        const Lanes<T, V> x1 = ldv<T, V>(x + (size_t)i1 * NB + l0);
+        const Lanes<T, V> x2 = ldv<T, V>(x + (size_t)i2 * NB + l0);
 #pragma unroll
-        for (int h = 0; h < V; ++h) acc[h] += wk * xk.v[h];
+        for (int h = 0; h < V; ++h) {
+            T t = w0 * x0.v[h];
+            if (nr > 1) t += w1 * x1.v[h];
+            if (nr > 2) t += w2 * x2.v[h];
+            acc[h] += t;
+        }
     }
 }
 
@@ -81,18 +95,60 @@ __device__ __forceinline__ void gather_lanes(T (&acc)[V], int kb, int ke, const 
         for (int h = 0; h < V; ++h)
             acc[h] += (w0.v[h] * x0.v[h] + w1.v[h] * x1.v[h]) + (w2.v[h] * x2.v[h] + w3.v[h] * x3.v[h]);
     }
-    for (; k < ke; ++k) {
-        const Lanes<T, V> wk = ldv<T, V>(wr + (size_t)k * NB);
-        const Lanes<T, V> xk = ldv<T, V>(x + (size_t)idx[k] * NB + l0);
+    if (k < ke) {
+        const int nr = ke - k;
+        const int k1 = nr > 1 ? k + 1 : k, k2 = nr > 2 ? k + 2 : k;
+        const int i0 = idx[k], i1 = idx[k1], i2 = idx[k2];
+        const Lanes<T, V> w0 = ldv<T, V>(wr + (size_t)k * NB);
+        const Lanes<T, V> w1 = ldv<T, V>(wr + (size_t)k1 * NB);
+        const Lanes<T, V> w2 = ldv<T, V>(wr + (size_t)k2 * NB);
+        const Lanes<T, V> x0 = ldv<T, V>(x + (size_t)i0 * NB + l0);
+        const Lanes<T, V> x1 = ldv<T, V>(x + (size_t)i1 * NB + l0);
+        const Lanes<T, V> x2 = ldv<T, V>(x + (size_t)i2 * NB + l0);
 #pragma unroll
-        for (int h = 0; h < V; ++h) acc[h] += wk.v[h] * xk.v[h];
+        for (int h = 0; h < V; ++h) {
+            T t = w0.v[h] * x0.v[h];
+            if (nr > 1) t += w1.v[h] * x1.v[h];
+            if (nr > 2) t += w2.v[h] * x2.v[h];
+            acc[h] += t;
+        }
     }
 }
 
-// Rows of a coarse level owned by block bid of the team: an even split.
-__device__ __forceinline__ void coarse_range(int n, int bid, int nblk, int* lo, int* hi) {
-    *lo = (int)((long long)n * bid / nblk);
-    *hi = (int)((long long)n * (bid + 1) / nblk);
+// First row r in [0, n] with cost[r] >= target (cost strictly increasing).
+__device__ __forceinline__ int cost_bound(const long long* cost, int n, long long target) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cost[mid] < target)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Rows of every coarse level owned by block bid of a team of nblk: equal
+// shares of the level's work (its prefix AmgLevel::cost), so that the long
+// rows around a mesh's high-degree nodes, which the aggregation numbers
+// first, do not all fall to one block.  Consecutive blocks' ranges tile
+// [0, n).  Called once per launch by all threads of the block (ends with a
+// block barrier); rng[0] is unused.
+__device__ __forceinline__ void amg_block_ranges(const AmgLevel* lvl, int levels, int bid, int nblk, int2* rng) {
+    const int t = threadIdx.x;
+    if (t < 2 * levels) {
+        const int l = t >> 1, side = t & 1;
+        int v = 0;
+        if (l >= 1) {
+            const AmgLevel& lv = lvl[l];
+            v = cost_bound(lv.cost, lv.n, lv.cost[lv.n] * (bid + side) / nblk);
+        }
+        if (side)
+            rng[l].y = v;
+        else
+            rng[l].x = v;
+    }
+    __syncthreads();
 }
 
 // 1 / D_l1 of row i of a level for this thread's lanes (per lane on special rows).
@@ -309,7 +365,7 @@ __device__ __noinline__ void amg_prolong(const AmgLevel& lc, const T* xc, T* y, 
 }
 
 // z = B r, one V-cycle (see above), on the team's rows: the block's own fine
-// rows [rs, re) and an even split of every coarse level.  r must be final on
+// rows [rs, re) and its share a.rng of every coarse level.  r must be final on
 // the block's own rows; z is final on them at return (the caller's barrier
 // publishes it).  Returns false if a team barrier timed out.
 template <typename T, int V>
@@ -341,7 +397,8 @@ __device__ bool amg_vcycle(const AmgCtx& a, const MeshDev& m, const AmgLevel* lv
     int lo = 0, hi = 0;
     for (int l = 1; l < L - 1; ++l) {
         const AmgLevel& lv = lvl[l];
-        coarse_range(lv.n, bid, nblk, &lo, &hi);
+        lo = a.rng[l].x;
+        hi = a.rng[l].y;
         amg_restrict<T, V>(lv, qprev, at(lv.off_b), at(lv.off_y), at(lv.off_l1), lo, hi, RB, rb, l0, NB);
         AMG_SYNC;
         amg_coarse_resid<T, V>(lv, at(lv.off_slot), at(lv.off_l1), 0, at(lv.off_y), at(lv.off_b), at(lv.off_q), lo, hi,
@@ -351,7 +408,8 @@ __device__ bool amg_vcycle(const AmgCtx& a, const MeshDev& m, const AmgLevel* lv
     }
     // coarsest level: amg_sweeps l1-Jacobi sweeps from zero
     const AmgLevel& lc = lvl[L - 1];
-    coarse_range(lc.n, bid, nblk, &lo, &hi);
+    lo = a.rng[L - 1].x;
+    hi = a.rng[L - 1].y;
     T* cur = at(lc.off_y);
     T* nxt = at(lc.off_q);
     amg_restrict<T, V>(lc, qprev, at(lc.off_b), cur, at(lc.off_l1), lo, hi, RB, rb, l0, NB);
@@ -366,7 +424,8 @@ __device__ bool amg_vcycle(const AmgCtx& a, const MeshDev& m, const AmgLevel* lv
     // up: y_l += P_{l+1} x_{l+1}, then x_l = y_l + (b_l - A_l y_l) / D_l1 (kept in q_l)
     for (int l = L - 2; l >= 1; --l) {
         const AmgLevel& lv = lvl[l];
-        coarse_range(lv.n, bid, nblk, &lo, &hi);
+        lo = a.rng[l].x;
+        hi = a.rng[l].y;
         AMG_SYNC;
         amg_prolong<T, V>(lvl[l + 1], xc, at(lv.off_y), lo + rb, hi, RB, l0, NB);
         AMG_SYNC;

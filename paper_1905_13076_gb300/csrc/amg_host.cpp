@@ -359,6 +359,17 @@ bool build_amg(int n, const int* rowptr, const int* col, const double* val, cons
         c.Rval = R.val;
         levels.push_back(std::move(c));
     }
+    for (size_t l = 1; l < levels.size(); ++l) {
+        AmgHostLevel& L = levels[l];
+        const AmgHostLevel* next = l + 1 < levels.size() ? &levels[l + 1] : nullptr;
+        L.cost.assign(L.n + 1, 0);
+        for (int c = 0; c < L.n; ++c) {
+            const long long a = L.rowptr[c + 1] - L.rowptr[c];
+            long long w = 2 * a * (L.row_slot[c] >= 0 ? 2 : 1) + (L.Rptr[c + 1] - L.Rptr[c]) + 4;
+            if (next) w += next->Pptr[c + 1] - next->Pptr[c];
+            L.cost[c + 1] = L.cost[c] + w;
+        }
+    }
     return true;
 }
 

@@ -39,6 +39,13 @@ struct AmgHostLevel {
     std::vector<double> slot_base;
     std::vector<int> cptr, csrc;
     std::vector<double> cw;
+    // l >= 1: [n + 1] prefix sums of each row's work in one V-cycle, so that
+    // a team can split the level into equal shares of work:
+    // cost(c) = 2 nnz_A(c) (1 + [c special]) + nnz_R(c) + nnz_P(l+1)(c) + 4
+    // (two residual passes, which also read per-lane values on a special
+    // row; the restriction; the prolongation from level l + 1; per-row
+    // loads and stores).  Strictly increasing from cost[0] = 0.
+    std::vector<long long> cost;
 };
 
 struct AmgOptions {

@@ -991,6 +991,9 @@ pppc_status setup_amg(pppc_handle* h) {
         TRY(upload(h, &Rcol, L.Rcol));
         TRY(upload(h, &cptr, L.cptr));
         TRY(upload(h, &csrc, L.csrc));
+        long long* cost;
+        TRY(upload(h, &cost, L.cost));
+        d.cost = cost;
         d.rowptr = rowptr;
         d.col = col;
         d.row_slot = row_slot;

@@ -96,6 +96,7 @@ struct AmgLevel {
     const int* cptr;           // [n_slots + 1]
     const int* csrc;           // slots of level l - 1
     const void* cw;            // (T)
+    const long long* cost;     // l >= 1: [n + 1] prefix of the rows' V-cycle work (amg_host.h)
 };
 
 // Arguments of the fine sweep of one lane team: the NB lanes lane0 ..

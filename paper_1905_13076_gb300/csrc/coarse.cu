@@ -216,7 +216,8 @@ __device__ bool cocg_amg_setup(const CocgArgs& a, const AmgLevel* lvl, int bid, 
         l1sp[(size_t)sp * NB + 2 * p + 1] = l1;
     }
     if (!grid_sync(a.bar, a.status, bid, nblk)) return false;
-    const AmgCtx ctx{NB, a.amg_levels, a.amg_sweeps, a.amg_ws, a.amg_J, a.bar, a.status, a.long_start, a.long_rows};
+    const AmgCtx ctx{NB,           a.amg_levels, a.amg_sweeps, a.amg_ws, a.amg_J, a.bar, a.status,
+                     a.long_start, a.long_rows,  nullptr};
     return amg_coarse_values<P, 2>(ctx, lvl, bid, nblk);
 }
 
@@ -224,8 +225,8 @@ __device__ bool cocg_amg_setup(const CocgArgs& a, const AmgLevel* lvl, int bid, 
 // caller's barrier) converted to P, one V-cycle, z converted back.  The
 // caller's barrier publishes z.
 template <typename T, typename P>
-__device__ bool cocg_amg_apply(const CocgArgs& a, const AmgLevel* lvl, const T* r, T* z, int bid, int nblk, int RB,
-                               int rb, int pl, double* s_red, double* s_tmp) {
+__device__ bool cocg_amg_apply(const CocgArgs& a, const AmgLevel* lvl, const int2* rng, const T* r, T* z, int bid,
+                               int nblk, int RB, int rb, int pl, double* s_red, double* s_tmp) {
     const MeshDev& m = a.mesh;
     const int H = a.H, NB = 2 * H;
     const int rs = a.row_start[bid], re = a.row_start[bid + 1];
@@ -238,7 +239,8 @@ __device__ bool cocg_amg_apply(const CocgArgs& a, const AmgLevel* lvl, const T* 
             rp[o] = (P)r[o];
             rp[o + 1] = (P)r[o + 1];
         }
-    const AmgCtx ctx{NB, a.amg_levels, a.amg_sweeps, a.amg_ws, a.amg_J, a.bar, a.status, a.long_start, a.long_rows};
+    const AmgCtx ctx{NB,           a.amg_levels, a.amg_sweeps, a.amg_ws, a.amg_J, a.bar, a.status,
+                     a.long_start, a.long_rows,  rng};
     if (!amg_vcycle<P, 2>(ctx, m, lvl, static_cast<const P*>(a.klinP), static_cast<const P*>(a.amg_J), rp, zp, bid,
                           nblk, re, rs + rb, RB, rb, l0, H, reinterpret_cast<P*>(s_red), reinterpret_cast<P*>(s_tmp)))
         return false;
@@ -299,10 +301,12 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
         for (int q = tid; q < words; q += blockDim.x) dst[q] = src[q];
         __syncthreads();
     }
+    __shared__ int2 s_rng[kAmgMaxLevels];
+    if (amg) amg_block_ranges(s_amg, a.amg_levels, bid, nblk, s_rng);
     // z = B r with the multigrid V-cycle (after a barrier that made r final)
     auto precondition = [&]() -> bool {
-        return a.amg_fp32 ? cocg_amg_apply<T, float>(a, s_amg, r, z, bid, nblk, RB, rb, pl, s_red, s_tmp)
-                          : cocg_amg_apply<T, double>(a, s_amg, r, z, bid, nblk, RB, rb, pl, s_red, s_tmp);
+        return a.amg_fp32 ? cocg_amg_apply<T, float>(a, s_amg, s_rng, r, z, bid, nblk, RB, rb, pl, s_red, s_tmp)
+                          : cocg_amg_apply<T, double>(a, s_amg, s_rng, r, z, bid, nblk, RB, rb, pl, s_red, s_tmp);
     };
 
     // init: x = p = s = 0, r = b, z = D^-1 r
@@ -339,14 +343,51 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
             const int kb = m.rowptr[i], ke = m.rowptr[i + 1], slot0 = m.row_slot[i];
             cplx wv = {0.0, 0.0};
             if (slot0 < 0) {
-                for (int kk = kb; kk < ke; ++kk) {
-                    const double kv = m.Klin[kk];
-                    const cplx zj = ldc<T>(z + 2 * ((size_t)m.col[kk] * H + pl));
-                    wv.re += kv * zj.re;
-                    wv.im += kv * zj.im;
+                // four gathers in flight: a block serves few rows per pass,
+                // so each thread's chain of loads sets the pace
+                int kk = kb;
+                for (; kk + 3 < ke; kk += 4) {
+                    const int c0 = m.col[kk], c1 = m.col[kk + 1], c2 = m.col[kk + 2], c3 = m.col[kk + 3];
+                    const double k0 = m.Klin[kk], k1 = m.Klin[kk + 1], k2 = m.Klin[kk + 2], k3 = m.Klin[kk + 3];
+                    const cplx z0 = ldc<T>(z + 2 * ((size_t)c0 * H + pl));
+                    const cplx z1 = ldc<T>(z + 2 * ((size_t)c1 * H + pl));
+                    const cplx z2 = ldc<T>(z + 2 * ((size_t)c2 * H + pl));
+                    const cplx z3 = ldc<T>(z + 2 * ((size_t)c3 * H + pl));
+                    wv.re += (k0 * z0.re + k1 * z1.re) + (k2 * z2.re + k3 * z3.re);
+                    wv.im += (k0 * z0.im + k1 * z1.im) + (k2 * z2.im + k3 * z3.im);
+                }
+                if (kk < ke) {   // the last 1-3 entries as one more group
+                    const int nr = ke - kk;
+                    const int k1 = nr > 1 ? kk + 1 : kk, k2 = nr > 2 ? kk + 2 : kk;
+                    const int c0 = m.col[kk], c1 = m.col[k1], c2 = m.col[k2];
+                    const double q0 = m.Klin[kk], q1 = m.Klin[k1], q2 = m.Klin[k2];
+                    const cplx z0 = ldc<T>(z + 2 * ((size_t)c0 * H + pl));
+                    const cplx z1 = ldc<T>(z + 2 * ((size_t)c1 * H + pl));
+                    const cplx z2 = ldc<T>(z + 2 * ((size_t)c2 * H + pl));
+                    double tr = q0 * z0.re, ti = q0 * z0.im;
+                    if (nr > 1) {
+                        tr += q1 * z1.re;
+                        ti += q1 * z1.im;
+                    }
+                    if (nr > 2) {
+                        tr += q2 * z2.re;
+                        ti += q2 * z2.im;
+                    }
+                    wv.re += tr;
+                    wv.im += ti;
                 }
             } else {
-                for (int kk = kb; kk < ke; ++kk) {
+                int kk = kb;
+                for (; kk + 1 < ke; kk += 2) {
+                    const int sl = slot0 + (kk - kb);
+                    const cplx z0 = ldc<T>(z + 2 * ((size_t)m.col[kk] * H + pl));
+                    const cplx z1 = ldc<T>(z + 2 * ((size_t)m.col[kk + 1] * H + pl));
+                    const double m0 = m.Mslot[sl] * a.inv_dT, m1 = m.Mslot[sl + 1] * a.inv_dT;
+                    const cplx a0 = {a.Kbar[sl] + cp.re * m0, cp.im * m0};
+                    const cplx a1 = {a.Kbar[sl + 1] + cp.re * m1, cp.im * m1};
+                    wv = cadd(wv, cadd(cmul(a0, z0), cmul(a1, z1)));
+                }
+                for (; kk < ke; ++kk) {
                     const int sl = slot0 + (kk - kb);
                     const double mv = m.Mslot[sl] * a.inv_dT;
                     const cplx av = {a.Kbar[sl] + cp.re * mv, cp.im * mv};
@@ -381,12 +422,24 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
         parity ^= 1;
 
         int act = 0;
+        // stop test: ||r_p||^2 <= tol^2 max(||b_p||^2, sum_q ||b_q||^2 / H).
+        // A harmonic that carries at least an average share of the right-hand
+        // side is solved to tol relative to its own; one whose right-hand
+        // side is far smaller (the even harmonics of a half-wave symmetric
+        // excitation hold only rounding noise) stops at tol times the
+        // average, where it no longer matters: sum_p ||r_p||^2 <= 2 tol^2
+        // sum_p ||b_p||^2 either way
+        double share = 0.0;
+        if (k == 0) {
+            for (int q = 0; q < H; ++q) share += s_sums[q];
+            share /= H;
+        }
         for (int l = tid; l < H; l += blockDim.x) {
             const double rho = s_sums[l];
             const cplx gam = {s_sums[H + l], s_sums[2 * H + l]};
             const cplx del = {s_sums[3 * H + l], s_sums[4 * H + l]};
             if (k == 0) {
-                s_stop[l] = a.tol * a.tol * rho;
+                s_stop[l] = a.tol * a.tol * fmax(rho, share);
                 s_act[l] = rho > 0.0;
             }
             int on = 0;
@@ -461,8 +514,13 @@ __device__ __forceinline__ void cocg_body(const CocgArgs& a, const int bid, cons
     }
 }
 
+// Single-instance launches: one block of up to kCocgThreads threads per SM
+// (H x floor(kCocgThreads / H) of them), so that a block serves as many rows
+// per pass as the register budget allows.
+constexpr int kCocgThreads = 1024;
+
 template <typename T>
-__global__ void __launch_bounds__(512) cocg_kernel(const CocgArgs a) {
+__global__ void __launch_bounds__(kCocgThreads) cocg_kernel(const CocgArgs a) {
     cocg_body<T>(a, blockIdx.x, gridDim.x);
 }
 
@@ -646,7 +704,7 @@ void launch_coarse_rhs(const MeshDev& m, int N, int NB, int H, double inv_dT, co
 
 cudaError_t cocg_config(bool fp32, int H, LaunchCfg* cfg) {
     if (H < 1 || H > 512) return cudaErrorInvalidValue;
-    const int threads = H * (512 / H);
+    const int threads = H * (kCocgThreads / H);
     const size_t smem = cocg_smem(H, threads);
     const void* fn = fp32 ? (const void*)cocg_kernel<float> : (const void*)cocg_kernel<double>;
     cudaError_t e = allow_max_dynamic_smem(fn);

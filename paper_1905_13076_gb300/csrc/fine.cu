@@ -636,8 +636,11 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
         for (int q = tid; q < words; q += blockDim.x) dst[q] = src[q];
         __syncthreads();
     }
+    __shared__ int2 s_rng[kAmgMaxLevels];
+    if (amg) amg_block_ranges(s_amg, a.amg_levels, bid, nblk, s_rng);
     T* l1f = amg ? static_cast<T*>(a.amg_ws) + s_amg[0].off_l1 * NB : nullptr;
-    const AmgCtx actx{NB, a.amg_levels, a.amg_sweeps, a.amg_ws, a.J, a.bar, a.status, a.long_start, a.long_rows};
+    const AmgCtx actx{NB,           a.amg_levels, a.amg_sweeps,  a.amg_ws, a.J, a.bar, a.status,
+                      a.long_start, a.long_rows,  s_rng};
     const long long n_elem_items = (long long)m.n_nl * NB;
     const long long gthreads = (long long)nblk * blockDim.x;
     // iteration counts, kept by thread 0: newton tests, pcg iterations, pcg

@@ -50,5 +50,6 @@ extern "C" int amg_field(int l, const char* name, void* out, int cap) {
     if (f == "cptr") return copy_out(L.cptr, out, cap);
     if (f == "csrc") return copy_out(L.csrc, out, cap);
     if (f == "cw") return copy_out(L.cw, out, cap);
+    if (f == "cost") return copy_out(L.cost, out, cap);
     return -1;
 }

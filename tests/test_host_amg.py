@@ -84,6 +84,7 @@ def build(lib, pat, a0, row_slot, coarse_rows=400):
         L = {k: field(lib, l, k, np.int32) for k in ("rowptr", "col", "row_slot", "sp_index", "Pptr", "Pcol",
                                                       "Rptr", "Rcol", "cptr", "csrc")}
         L.update({k: field(lib, l, k, np.float64) for k in ("val", "l1", "Pval", "Rval", "slot_base", "cw")})
+        L["cost"] = field(lib, l, "cost", np.int64)
         n = len(L["rowptr"]) - 1
         L["A"] = sp.csr_matrix((L["val"], L["col"], L["rowptr"]), shape=(n, n))
         if l > 0:
@@ -151,6 +152,24 @@ def test_lane_tables_rebuild_the_lane_galerkin_products(small):
         fine_sp = levels[l - 1]["row_slot"] >= 0
         reach = np.asarray(abs(P[fine_sp]).sum(axis=0)).ravel() > 0
         assert ((levels[l]["row_slot"] >= 0) == reach).all()
+
+
+def test_work_prefix_counts_each_rows_vcycle_work(small):
+    """Every coarse level carries the prefix of its rows' V-cycle work, the
+    key of the split of its rows among a team's blocks: two residual passes
+    (twice the reads on a special row), the restriction row, the row of the
+    next level's prolongation, and 4 per row."""
+    levels = small[-1]
+    assert len(levels[0]["cost"]) == 0
+    for l in range(1, len(levels)):
+        L = levels[l]
+        nnz_a = np.diff(L["rowptr"])
+        w = 2 * nnz_a * (1 + (L["row_slot"] >= 0)) + np.diff(L["Rptr"]) + 4
+        if l + 1 < len(levels):
+            w = w + np.diff(levels[l + 1]["Pptr"])
+        assert L["cost"][0] == 0 and len(L["cost"]) == len(nnz_a) + 1
+        np.testing.assert_array_equal(np.diff(L["cost"]), w)
+        assert (np.diff(L["cost"]) > 0).all()
 
 
 def vcycle(levels, mats, r, sweeps=2):

@@ -180,3 +180,65 @@ def test_noalloc_reports_the_iteration_cap(lib):
     assert st == 5, lib.pppc_status_string(st)            # PPPC_ERR_LINEAR
     st, its = _call(lib, t, tol=1e-12, max_it=100)
     assert st == 0 and 1 < its <= 100
+
+
+def test_harmonic_stop_rule_skips_noise_level_harmonics(lib):
+    """The harmonic solves stop harmonic p at ||r_p||^2 <= tol^2 max(||b_p||^2,
+    sum_q ||b_q||^2 / (N/2+1)): harmonics that carry the right-hand side are
+    solved to tol relative to their own, and harmonics holding only rounding
+    noise (the even harmonics of a half-wave symmetric excitation) stop at
+    once instead of chasing their noise.  Checked with residuals recomputed
+    here from the returned x: the same iteration count as with the noise set
+    to zero, each harmonic within its bound, and the sum within 2 tol^2."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    n, N, tol = 40, 8, 1e-6
+    H = N // 2 + 1
+    rows = np.repeat(np.arange(n), 3)
+    cols = rows + np.tile([-1, 0, 1], n)
+    keep = (cols >= 0) & (cols < n)
+    rows, cols = rows[keep], cols[keep]
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=n))]).astype(np.int32)
+    kval = np.where(rows == cols, 2.01, -1.0)
+    cval = np.where(rows == cols, 1.0, 0.1)
+    rng = np.random.default_rng(11)
+    scale = np.array([1e-14, 1.0, 1e-14, 0.7, 1e-14])    # p = 0..4; p = 1 and 3 above the average
+    bc = (rng.standard_normal((n, H)) + 1j * rng.standard_normal((n, H))) * scale
+    bc[:, 0] = bc[:, 0].real                              # p = 0 and N/2 of a real signal are real
+    bc[:, N // 2] = bc[:, N // 2].real
+
+    def solve(b_complex):
+        b = np.empty((n, 2 * H))
+        b[:, 0::2], b[:, 1::2] = b_complex.real, b_complex.imag
+        t = {k: torch.from_numpy(v).to(dev) for k, v in
+             dict(rowptr=rowptr, col=cols.astype(np.int32), kval=kval, cval=cval, b=b).items()}
+        t["x"] = torch.zeros(n, 2 * H, dtype=torch.float64, device=dev)
+        its = ctypes.c_int32(-1)
+        st = lib.pppc_harmonic_solve_noalloc(n, t["rowptr"].data_ptr(), t["col"].data_ptr(), t["kval"].data_ptr(),
+                                             t["cval"].data_ptr(), N, t["b"].data_ptr(), t["x"].data_ptr(), tol, 500,
+                                             None, ctypes.byref(its))
+        assert st == 0, lib.pppc_status_string(st)
+        x = t["x"].cpu().numpy()
+        return x[:, 0::2] + 1j * x[:, 1::2], its.value
+
+    x, its = solve(bc)
+    clean = bc.copy()
+    clean[:, scale < 1e-10] = 0.0
+    _, its_clean = solve(clean)
+    assert its == its_clean
+    K = np.zeros((n, n))
+    C = np.zeros((n, n))
+    K[rows, cols] = kval
+    C[rows, cols] = cval
+    r2 = np.empty(H)
+    b2 = (abs(bc) ** 2).sum(axis=0)
+    for p in range(H):
+        A = K + (1.0 - np.exp(-2j * np.pi * p / N)) * C
+        r2[p] = (abs(bc[:, p] - A @ x[:, p]) ** 2).sum()
+    bound = tol ** 2 * np.maximum(b2, b2.sum() / H)
+    assert (r2 <= 1.01 * bound).all(), (r2, bound)
+    assert r2.sum() <= 2 * tol ** 2 * b2.sum()
+    # the carrying harmonics (each above the average share) are solved to tol of their own right-hand side
+    assert (b2[[1, 3]] > b2.sum() / H).all()
+    assert r2[1] <= 1.01 * tol ** 2 * b2[1] and r2[3] <= 1.01 * tol ** 2 * b2[3]
