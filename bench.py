@@ -386,7 +386,7 @@ LARGE_LEVELS = 4   # fine implicit-Euler levels of every subinterval per timed s
 # workload's N = 256 (working set above L2): 571.9 GB over 124 501 rows x
 # 33 920 lane-iterations.  The traffic grows in proportion to rows and
 # lane-iterations once the working set exceeds L2.
-TRAFFIC_PER_ROW_LANE_ITER = 134.1
+TRAFFIC_PER_ROW_LANE_ITER = 136.9
 LARGE_DESC = ("coax large: nr=500 x ntheta=1000 (499001 DOFs), N=256, 200 fine steps, sigma=3e7, Brauer steel, "
               "40 A @ 50 Hz + 8 A @ 150 Hz")
 

@@ -37,19 +37,20 @@ struct AmgCtx {
 // team's workspace; team barriers separate the steps that read other
 // blocks' rows.
 
-// acc += sum_{k in [kb, ke)} w[k] x[idx[k]] for this thread's V lanes, with
-// shared scalar weights; four gathers are issued before any is consumed
-// (the rows of the coarse levels and of R are long, and a gather that waits
-// for its index and then its vector would serialise on memory latency), and
-// the last 1-3 entries form one more such group (a 7-entry fine row takes
-// two rounds of loads, not four); its unused places reload entry k.
+// acc += sum_k w[k] x[idx[k]] over k = kb, kb + S, kb + 2S, ... < ke (S = 1:
+// the whole row) for this thread's V lanes, with shared scalar weights; four
+// gathers are issued before any is consumed (the rows of the coarse levels
+// and of R are long, and a gather that waits for its index and then its
+// vector would serialise on memory latency), and the last 1-3 entries form
+// one more such group (a 7-entry fine row takes two rounds of loads, not
+// four); its unused places reload the group's first entry.
 template <typename T, int V>
 __device__ __forceinline__ void gather_shared(T (&acc)[V], int kb, int ke, const int* __restrict__ idx,
-                                              const T* __restrict__ w, const T* x, int NB, int l0) {
+                                              const T* __restrict__ w, const T* x, int NB, int l0, int S = 1) {
     int k = kb;
-    for (; k + 3 < ke; k += 4) {
-        const int i0 = idx[k], i1 = idx[k + 1], i2 = idx[k + 2], i3 = idx[k + 3];
-        const T w0 = w[k], w1 = w[k + 1], w2 = w[k + 2], w3 = w[k + 3];
+    for (; k + 3 * S < ke; k += 4 * S) {
+        const int i0 = idx[k], i1 = idx[k + S], i2 = idx[k + 2 * S], i3 = idx[k + 3 * S];
+        const T w0 = w[k], w1 = w[k + S], w2 = w[k + 2 * S], w3 = w[k + 3 * S];
         const Lanes<T, V> x0 = ldv<T, V>(x + (size_t)i0 * NB + l0);
         const Lanes<T, V> x1 = ldv<T, V>(x + (size_t)i1 * NB + l0);
         const Lanes<T, V> x2 = ldv<T, V>(x + (size_t)i2 * NB + l0);
@@ -58,8 +59,8 @@ __device__ __forceinline__ void gather_shared(T (&acc)[V], int kb, int ke, const
         for (int h = 0; h < V; ++h) acc[h] += (w0 * x0.v[h] + w1 * x1.v[h]) + (w2 * x2.v[h] + w3 * x3.v[h]);
     }
     if (k < ke) {
-        const int nr = ke - k;
-        const int k1 = nr > 1 ? k + 1 : k, k2 = nr > 2 ? k + 2 : k;
+        const bool h1 = k + S < ke, h2 = k + 2 * S < ke;
+        const int k1 = h1 ? k + S : k, k2 = h2 ? k + 2 * S : k;
         const int i0 = idx[k], i1 = idx[k1], i2 = idx[k2];
         const T w0 = w[k], w1 = w[k1], w2 = w[k2];
         const Lanes<T, V> x0 = ldv<T, V>(x + (size_t)i0 * NB + l0);
@@ -68,8 +69,8 @@ __device__ __forceinline__ void gather_shared(T (&acc)[V], int kb, int ke, const
 #pragma unroll
         for (int h = 0; h < V; ++h) {
             T t = w0 * x0.v[h];
-            if (nr > 1) t += w1 * x1.v[h];
-            if (nr > 2) t += w2 * x2.v[h];
+            if (h1) t += w1 * x1.v[h];
+            if (h2) t += w2 * x2.v[h];
             acc[h] += t;
         }
     }
@@ -78,15 +79,15 @@ __device__ __forceinline__ void gather_shared(T (&acc)[V], int kb, int ke, const
 // Same with per-lane weights wl[(s0 + k - kb) NB + l0 ..] (a special row's slots).
 template <typename T, int V>
 __device__ __forceinline__ void gather_lanes(T (&acc)[V], int kb, int ke, const int* __restrict__ idx, const T* wl,
-                                             int s0, const T* x, int NB, int l0) {
+                                             int s0, const T* x, int NB, int l0, int S = 1) {
     const T* wr = wl + (size_t)(s0 - kb) * NB + l0;
     int k = kb;
-    for (; k + 3 < ke; k += 4) {
-        const int i0 = idx[k], i1 = idx[k + 1], i2 = idx[k + 2], i3 = idx[k + 3];
+    for (; k + 3 * S < ke; k += 4 * S) {
+        const int i0 = idx[k], i1 = idx[k + S], i2 = idx[k + 2 * S], i3 = idx[k + 3 * S];
         const Lanes<T, V> w0 = ldv<T, V>(wr + (size_t)k * NB);
-        const Lanes<T, V> w1 = ldv<T, V>(wr + (size_t)(k + 1) * NB);
-        const Lanes<T, V> w2 = ldv<T, V>(wr + (size_t)(k + 2) * NB);
-        const Lanes<T, V> w3 = ldv<T, V>(wr + (size_t)(k + 3) * NB);
+        const Lanes<T, V> w1 = ldv<T, V>(wr + (size_t)(k + S) * NB);
+        const Lanes<T, V> w2 = ldv<T, V>(wr + (size_t)(k + 2 * S) * NB);
+        const Lanes<T, V> w3 = ldv<T, V>(wr + (size_t)(k + 3 * S) * NB);
         const Lanes<T, V> x0 = ldv<T, V>(x + (size_t)i0 * NB + l0);
         const Lanes<T, V> x1 = ldv<T, V>(x + (size_t)i1 * NB + l0);
         const Lanes<T, V> x2 = ldv<T, V>(x + (size_t)i2 * NB + l0);
@@ -96,8 +97,8 @@ __device__ __forceinline__ void gather_lanes(T (&acc)[V], int kb, int ke, const 
             acc[h] += (w0.v[h] * x0.v[h] + w1.v[h] * x1.v[h]) + (w2.v[h] * x2.v[h] + w3.v[h] * x3.v[h]);
     }
     if (k < ke) {
-        const int nr = ke - k;
-        const int k1 = nr > 1 ? k + 1 : k, k2 = nr > 2 ? k + 2 : k;
+        const bool h1 = k + S < ke, h2 = k + 2 * S < ke;
+        const int k1 = h1 ? k + S : k, k2 = h2 ? k + 2 * S : k;
         const int i0 = idx[k], i1 = idx[k1], i2 = idx[k2];
         const Lanes<T, V> w0 = ldv<T, V>(wr + (size_t)k * NB);
         const Lanes<T, V> w1 = ldv<T, V>(wr + (size_t)k1 * NB);
@@ -108,11 +109,48 @@ __device__ __forceinline__ void gather_lanes(T (&acc)[V], int kb, int ke, const 
 #pragma unroll
         for (int h = 0; h < V; ++h) {
             T t = w0.v[h] * x0.v[h];
-            if (nr > 1) t += w1.v[h] * x1.v[h];
-            if (nr > 2) t += w2.v[h] * x2.v[h];
+            if (h1) t += w1.v[h] * x1.v[h];
+            if (h2) t += w2.v[h] * x2.v[h];
             acc[h] += t;
         }
     }
+}
+
+// Row groups per row on a coarse level: a block owns `rows` rows and RB row
+// groups of G threads.  When the rows are few against RB (the deep levels,
+// where a row is long and most groups would idle), S groups of one warp
+// share a row, each summing every S-th entry, and combine with shuffles.  S
+// is a power of two with S G dividing 32 (G must divide 32: otherwise 1).
+// Each doubling is taken only if it shortens the longest queue of row
+// shares, ceil(rows / (RB / S)) / S, by 10% or more: with many rows per
+// group the ceilings differ by a row at most, and a split row pays its
+// per-row loads and the shuffles S times.
+__device__ __forceinline__ int row_split(int rows, int RB, int G) {
+    if (G <= 0 || 32 % G != 0 || rows <= 0) return 1;
+    int best = 1;
+    long long best_q = (rows + RB - 1) / RB;
+    for (int S = 2; S * G <= 32 && RB % S == 0; S <<= 1) {
+        const int segs = RB / S;
+        const long long q = (rows + segs - 1) / segs;
+        if (10 * q * best > 9 * best_q * S) break;
+        best = S;
+        best_q = q;
+    }
+    return best;
+}
+
+// acc summed over the S row groups of this thread's segment (xor butterfly
+// over lane offsets G, 2G, ..., within one warp); every lane ends with the
+// row's sum.
+template <typename T, int V>
+__device__ __forceinline__ void segment_sum(T (&acc)[V], int S, int G) {
+    if (S == 1) return;
+    const int width = S * G;
+    const int lane = threadIdx.x & 31;
+    const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u) << (lane & ~(width - 1));
+    for (int o = G; o < width; o <<= 1)
+#pragma unroll
+        for (int h = 0; h < V; ++h) acc[h] += __shfl_xor_sync(mask, acc[h], o);
 }
 
 // First row r in [0, n] with cost[r] >= target (cost strictly increasing).
@@ -297,15 +335,25 @@ template <typename T, int V>
 __device__ __noinline__ void amg_coarse_resid(const AmgLevel& lv, const T* slots, const T* l1sp, int mode, const T* x,
                                               const T* b, T* out, int lo, int hi, int RB, int rb, int l0, int NB) {
     const T* val = static_cast<const T*>(lv.val);
-    for (int c = lo + rb; c < hi; c += RB) {
+    const int G = NB / V, S = row_split(hi - lo, RB, G), seg = rb / S, sub = rb - seg * S, NS = RB / S;
+    for (int c = lo + seg; c < hi; c += NS) {
         const int kb = lv.rowptr[c], ke = lv.rowptr[c + 1], s0 = lv.row_slot[c];
         T acc[V];
 #pragma unroll
         for (int h = 0; h < V; ++h) acc[h] = 0;
-        if (s0 < 0)
-            gather_shared<T, V>(acc, kb, ke, lv.col, val, x, NB, l0);
-        else
-            gather_lanes<T, V>(acc, kb, ke, lv.col, slots, s0, x, NB, l0);
+        if (S == 1) {   // the whole row: the stride folds away
+            if (s0 < 0)
+                gather_shared<T, V>(acc, kb, ke, lv.col, val, x, NB, l0);
+            else
+                gather_lanes<T, V>(acc, kb, ke, lv.col, slots, s0, x, NB, l0);
+        } else {
+            if (s0 < 0)
+                gather_shared<T, V>(acc, kb + sub, ke, lv.col, val, x, NB, l0, S);
+            else
+                gather_lanes<T, V>(acc, kb + sub, ke, lv.col, slots + (size_t)sub * NB, s0, x, NB, l0, S);
+            segment_sum<T, V>(acc, S, G);
+        }
+        if (sub != 0) continue;
         const size_t o = (size_t)c * NB + l0;
         const Lanes<T, V> bi = ldv<T, V>(b + o);
         Lanes<T, V> res;
@@ -327,11 +375,18 @@ template <typename T, int V>
 __device__ __noinline__ void amg_restrict(const AmgLevel& lv, const T* q, T* b, T* y, const T* l1sp, int lo, int hi,
                                           int RB, int rb, int l0, int NB) {
     const T* Rv = static_cast<const T*>(lv.Rval);
-    for (int c = lo + rb; c < hi; c += RB) {
+    const int G = NB / V, S = row_split(hi - lo, RB, G), seg = rb / S, sub = rb - seg * S, NS = RB / S;
+    for (int c = lo + seg; c < hi; c += NS) {
         T acc[V];
 #pragma unroll
         for (int h = 0; h < V; ++h) acc[h] = 0;
-        gather_shared<T, V>(acc, lv.Rptr[c], lv.Rptr[c + 1], lv.Rcol, Rv, q, NB, l0);
+        if (S == 1) {
+            gather_shared<T, V>(acc, lv.Rptr[c], lv.Rptr[c + 1], lv.Rcol, Rv, q, NB, l0);
+        } else {
+            gather_shared<T, V>(acc, lv.Rptr[c] + sub, lv.Rptr[c + 1], lv.Rcol, Rv, q, NB, l0, S);
+            segment_sum<T, V>(acc, S, G);
+        }
+        if (sub != 0) continue;
         const size_t o = (size_t)c * NB + l0;
         const Lanes<T, V> d = inv_l1<T, V>(lv, l1sp, c, NB, l0);
         Lanes<T, V> bv, yv;
