@@ -569,7 +569,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
     double* s_beta = s_alpha + NB;
     double* s_rprev = s_beta + NB; // ||R|| at the previous Newton test
     double* s_eta = s_rprev + NB;  // previous forcing term
-    double* s_coef = s_eta + NB;   // this round's update u += coef * (x or dx), see below
+    double* s_coef = s_eta + NB;   // this Newton iteration's update u += coef * (x or dx), see below
     double* s_lam = s_coef + NB;   // fraction of the last Newton step dx now applied
     RT* s_red = reinterpret_cast<RT*>(s_lam + NB);   // [NV][red_slots(G)][NB]
     RT* s_sums = s_red + NV * red_slots(G, blockDim.x) * NB;  // [NV][NB], identical in every block
@@ -1023,7 +1023,7 @@ __device__ __forceinline__ void fine_sweep_body(const FineArgs& a, const int bid
                 }
                 if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             }
-            // ---- own rows: apply this round's steps, then element data at the new u
+            // ---- own rows: apply this iteration's steps, then element data at the new u
             apply_steps<T, V>(u, LD, xB, vo, static_cast<T*>(a.dx), s_eta + NB, row0, re, RB, l0, NB);
             if (!grid_sync(a.bar, a.status, bid, nblk)) return;
             if (!a.adjoint) {
