@@ -383,8 +383,8 @@ def pcg_bytes_per_row_lane(mixed: bool, special_frac: float, nnz_row: float, NB:
 LARGE_LEVELS = 4   # fine implicit-Euler levels of every subinterval per timed step
 # DRAM bytes (read + written) per row and lane-iteration of the multigrid
 # fine team kernel, measured with ncu on a 250 x 500 mesh with the large
-# workload's N = 256 (working set above L2): 571.9 GB over 124 501 rows x
-# 33 920 lane-iterations.  The traffic grows in proportion to rows and
+# workload's N = 256 (working set above L2): 579.1 GB over 124 501 rows x
+# 33 968 lane-iterations.  The traffic grows in proportion to rows and
 # lane-iterations once the working set exceeds L2.
 TRAFFIC_PER_ROW_LANE_ITER = 136.9
 LARGE_DESC = ("coax large: nr=500 x ntheta=1000 (499001 DOFs), N=256, 200 fine steps, sigma=3e7, Brauer steel, "
@@ -953,7 +953,10 @@ def main():
     mc = solver.mesh_counts()
     nnz_row = mc["nnz"] / mc["ndof"]
     sp_frac = mc["special_rows"] / mc["ndof"]
-    bpr = pcg_bytes_per_row_lane(mixed, sp_frac, nnz_row, prob.N, tri=args.precond == "tridiag")
+    if args.precond == "amg":
+        bpr = fine_bytes_per_row_lane_round(mixed, sp_frac, prob.N, solver.fine_plan()["amg_rows"])["total"]
+    else:
+        bpr = pcg_bytes_per_row_lane(mixed, sp_frac, nnz_row, prob.N, tri=args.precond == "tridiag")
     fine_s = sum(fine_ms) * 1e-3
     pcg_bytes = bpr * ndof * prob.N * pcg
     hbm_peak, peak_src = peaks()
