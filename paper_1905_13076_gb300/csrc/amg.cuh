@@ -420,7 +420,10 @@ __device__ __noinline__ void amg_prolong(const AmgLevel& lc, const T* xc, T* y, 
 }
 
 // z = B r, one V-cycle (see above), on the team's rows: the block's own fine
-// rows [rs, re) and its share a.rng of every coarse level.  r must be final on
+// rows [rs, re) and its share a.rng of every coarse level.  Every thread of
+// the block must belong to a row group (blockDim a multiple of G = NB / V):
+// a thread with rb >= RB would repeat another group's rows, and the
+// prolongation's y += P x would then add twice.  r must be final on
 // the block's own rows; z is final on them at return (the caller's barrier
 // publishes it).  Returns false if a team barrier timed out.
 template <typename T, int V>

@@ -223,7 +223,10 @@ __device__ bool cocg_amg_setup(const CocgArgs& a, const AmgLevel* lvl, int bid, 
 
 // z = B r on the block's contiguous rows: r (FP64, final on every row: the
 // caller's barrier) converted to P, one V-cycle, z converted back.  The
-// caller's barrier publishes z.
+// caller's barrier publishes z.  The V-cycle needs blockDim to be a multiple
+// of H (cocg_config's single-instance launches are; the batched launch's
+// 512-thread blocks are not, and its members' solves take no multigrid
+// arguments: cocg_args).
 template <typename T, typename P>
 __device__ bool cocg_amg_apply(const CocgArgs& a, const AmgLevel* lvl, const int2* rng, const T* r, T* z, int bid,
                                int nblk, int RB, int rb, int pl, double* s_red, double* s_tmp) {
