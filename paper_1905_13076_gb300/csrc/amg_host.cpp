@@ -194,10 +194,16 @@ void coarse_level(const AmgHostLevel& f, const Csr& P, const Csr& Ac, AmgHostLev
     // contributions (coarse slot <- weight * fine slot), counted then filled
     // per coarse slot: for special fine row i, entry (i, j) = fine slot s,
     // P(i, a) and P(j, b) give weight P(i, a) P(j, b) to coarse entry (a, b)
-    auto cslot = [&](int a, int b) {
-        const int* lo = c.col.data() + c.rowptr[a];
-        const int* hi = c.col.data() + c.rowptr[a + 1];
-        return c.row_slot[a] + (int)(std::lower_bound(lo, hi, b) - lo);
+    // coarse row a's slot of column b: a dense map over the columns of the
+    // row last loaded (every column looked up lies in that row's pattern,
+    // the Galerkin product's, so stale entries of other columns are never
+    // read)
+    std::vector<int> pos(c.n, 0);
+    int loaded = -1;
+    auto load_row = [&](int a) {
+        if (a == loaded) return;
+        for (int k = c.rowptr[a]; k < c.rowptr[a + 1]; ++k) pos[c.col[k]] = c.row_slot[a] + (k - c.rowptr[a]);
+        loaded = a;
     };
     std::vector<int64_t> cnt((size_t)slots + 1, 0);
     for (int pass = 0; pass < 2; ++pass) {
@@ -213,11 +219,12 @@ void coarse_level(const AmgHostLevel& f, const Csr& P, const Csr& Ac, AmgHostLev
             for (int p = P.ptr[i]; p < P.ptr[i + 1]; ++p) {
                 const int a = P.col[p];
                 const double pa = P.val[p];
+                load_row(a);
                 for (int k = f.rowptr[i]; k < f.rowptr[i + 1]; ++k) {
                     const int j = f.col[k];
                     const int s = f.row_slot[i] + (k - f.rowptr[i]);
                     for (int q = P.ptr[j]; q < P.ptr[j + 1]; ++q) {
-                        const int e = cslot(a, P.col[q]);
+                        const int e = pos[P.col[q]];
                         if (pass == 0)
                             ++cnt[e + 1];
                         else
@@ -227,15 +234,23 @@ void coarse_level(const AmgHostLevel& f, const Csr& P, const Csr& Ac, AmgHostLev
             }
         }
         if (pass == 0) continue;
-        // per coarse slot: sort by source slot, merge duplicates
+        // per coarse slot: sort by source slot, merge duplicates.  The fill
+        // visits the fine rows and their entries in order, so a slot's
+        // contributions arrive sorted whenever the fine level numbers its
+        // slots row by row (the mesh and every coarse level do), and one
+        // fine slot reaches a coarse slot at most once (P's rows hold
+        // distinct columns): the sort is then skipped and nothing merges.
         c.cptr.assign(slots + 1, 0);
         c.csrc.clear();
         c.cw.clear();
+        c.csrc.reserve(items.size());
+        c.cw.reserve(items.size());
+        const auto by_src = [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+            return x.first < y.first;
+        };
         for (int e = 0; e < slots; ++e) {
             auto b = items.begin() + cnt[e], en = items.begin() + cnt[e + 1];
-            std::sort(b, en, [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
-                return x.first < y.first;
-            });
+            if (!std::is_sorted(b, en, by_src)) std::sort(b, en, by_src);
             for (auto it = b; it != en; ++it) {
                 if (!c.csrc.empty() && (int)c.csrc.size() > c.cptr[e] && c.csrc.back() == it->first)
                     c.cw.back() += it->second;
