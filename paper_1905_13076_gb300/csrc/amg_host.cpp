@@ -208,10 +208,10 @@ void coarse_level(const AmgHostLevel& f, const Csr& P, const Csr& Ac, AmgHostLev
     std::vector<int64_t> cnt((size_t)slots + 1, 0);
     for (int pass = 0; pass < 2; ++pass) {
         std::vector<int64_t> fillpos;
-        std::vector<std::pair<int, double>> items;
         if (pass == 1) {
             for (int e = 0; e < slots; ++e) cnt[e + 1] += cnt[e];
-            items.resize((size_t)cnt[slots]);
+            c.csrc.assign((size_t)cnt[slots], 0);
+            c.cw.assign((size_t)cnt[slots], 0.0);
             fillpos.assign(cnt.begin(), cnt.end() - 1);
         }
         for (int i = 0; i < f.n; ++i) {
@@ -225,43 +225,61 @@ void coarse_level(const AmgHostLevel& f, const Csr& P, const Csr& Ac, AmgHostLev
                     const int s = f.row_slot[i] + (k - f.rowptr[i]);
                     for (int q = P.ptr[j]; q < P.ptr[j + 1]; ++q) {
                         const int e = pos[P.col[q]];
-                        if (pass == 0)
+                        if (pass == 0) {
                             ++cnt[e + 1];
-                        else
-                            items[(size_t)fillpos[e]++] = {s, pa * P.val[q]};
+                        } else {
+                            const size_t w = (size_t)fillpos[e]++;
+                            c.csrc[w] = s;
+                            c.cw[w] = pa * P.val[q];
+                        }
                     }
                 }
             }
         }
-        if (pass == 0) continue;
-        // per coarse slot: sort by source slot, merge duplicates.  The fill
-        // visits the fine rows and their entries in order, so a slot's
-        // contributions arrive sorted whenever the fine level numbers its
-        // slots row by row (the mesh and every coarse level do), and one
-        // fine slot reaches a coarse slot at most once (P's rows hold
-        // distinct columns): the sort is then skipped and nothing merges.
-        c.cptr.assign(slots + 1, 0);
-        c.csrc.clear();
-        c.cw.clear();
-        c.csrc.reserve(items.size());
-        c.cw.reserve(items.size());
-        const auto by_src = [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
-            return x.first < y.first;
-        };
-        for (int e = 0; e < slots; ++e) {
-            auto b = items.begin() + cnt[e], en = items.begin() + cnt[e + 1];
-            if (!std::is_sorted(b, en, by_src)) std::sort(b, en, by_src);
-            for (auto it = b; it != en; ++it) {
-                if (!c.csrc.empty() && (int)c.csrc.size() > c.cptr[e] && c.csrc.back() == it->first)
-                    c.cw.back() += it->second;
-                else {
-                    c.csrc.push_back(it->first);
-                    c.cw.push_back(it->second);
+    }
+    // per coarse slot: sorted by source slot, duplicates merged, compacted in
+    // place.  The fill visits the fine rows and their entries in order, so a
+    // slot's contributions arrive sorted whenever the fine level numbers its
+    // slots row by row (the mesh and every coarse level do), and one fine
+    // slot reaches a coarse slot at most once (P's rows hold distinct
+    // columns): such a slot is kept as filled.  Any other is sorted and
+    // merged; merging only shrinks, so the write position never passes the
+    // read position.
+    c.cptr.assign(slots + 1, 0);
+    const auto by_src = [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+        return x.first < y.first;
+    };
+    std::vector<std::pair<int, double>> tmp;
+    size_t w = 0;
+    for (int e = 0; e < slots; ++e) {
+        const size_t b = (size_t)cnt[e], en = (size_t)cnt[e + 1];
+        bool increasing = true;
+        for (size_t r = b + 1; r < en && increasing; ++r) increasing = c.csrc[r - 1] < c.csrc[r];
+        if (increasing) {
+            if (w != b)
+                for (size_t r = b; r < en; ++r) {
+                    c.csrc[w + (r - b)] = c.csrc[r];
+                    c.cw[w + (r - b)] = c.cw[r];
+                }
+            w += en - b;
+        } else {
+            tmp.clear();
+            for (size_t r = b; r < en; ++r) tmp.emplace_back(c.csrc[r], c.cw[r]);
+            if (!std::is_sorted(tmp.begin(), tmp.end(), by_src)) std::sort(tmp.begin(), tmp.end(), by_src);
+            for (const auto& x : tmp) {
+                if (w > (size_t)c.cptr[e] && c.csrc[w - 1] == x.first) {
+                    c.cw[w - 1] += x.second;
+                } else {
+                    c.csrc[w] = x.first;
+                    c.cw[w] = x.second;
+                    ++w;
                 }
             }
-            c.cptr[e + 1] = (int)c.csrc.size();
         }
+        c.cptr[e + 1] = (int)w;
     }
+    c.csrc.resize(w);
+    c.cw.resize(w);
     // base: the representative Galerkin value minus what the tabulated
     // contributions give at the representative fine values
     std::vector<double> fslot((size_t)f.n_slots, 0.0);

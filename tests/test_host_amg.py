@@ -101,7 +101,11 @@ def lane_matrices(levels, jv):
     L0 = levels[0]
     sp0 = L0["row_slot"] >= 0
     k0 = np.repeat(sp0, np.diff(L0["rowptr"]))
-    slots = jv[k0]                                       # level 0 slots: the lane's special-row entries
+    # level 0 slots: the lane's special-row entries, at their slot numbers
+    rows = np.repeat(np.arange(len(sp0)), np.diff(L0["rowptr"]))[k0]
+    kk = np.nonzero(k0)[0]
+    slots = np.empty(int(k0.sum()))
+    slots[L0["row_slot"][rows] + (kk - L0["rowptr"][rows])] = jv[k0]
     mats = [sp.csr_matrix((np.where(k0, jv, L0["val"]), L0["col"], L0["rowptr"]), shape=L0["A"].shape)]
     for L in levels[1:]:
         owner = np.repeat(np.arange(len(L["slot_base"])), np.diff(L["cptr"]))
@@ -170,6 +174,26 @@ def test_work_prefix_counts_each_rows_vcycle_work(small):
         assert L["cost"][0] == 0 and len(L["cost"]) == len(nnz_a) + 1
         np.testing.assert_array_equal(np.diff(L["cost"]), w)
         assert (np.diff(L["cost"]) > 0).all()
+
+
+def test_tables_do_not_depend_on_the_fine_slot_order(amglib):
+    """With the fine special rows' slots numbered in reverse row order (every
+    coarse slot's contributions then arrive out of order and are sorted), the
+    tables still rebuild P^T J P at every level."""
+    pat, a0, jv, row_slot, special = problem("small")
+    lens = np.diff(pat[0])
+    rs = np.full(len(lens), -1, dtype=np.int32)
+    rows = np.nonzero(special)[0][::-1]
+    rs[rows] = np.concatenate([[0], np.cumsum(lens[rows])[:-1]]).astype(np.int32)
+    levels = build(amglib, pat, a0, rs, coarse_rows=40)
+    assert len(levels) >= 3
+    mats = lane_matrices(levels, jv)
+    for l in range(1, len(levels)):
+        P = levels[l]["P"]
+        assert rel(mats[l], (P.T @ mats[l - 1] @ P).tocsr()) < 1e-12, l
+        cptr, csrc = levels[l]["cptr"], levels[l]["csrc"]
+        for e in range(len(cptr) - 1):                   # sorted, merged per coarse slot
+            assert (np.diff(csrc[cptr[e]:cptr[e + 1]]) > 0).all()
 
 
 def vcycle(levels, mats, r, sweeps=2):
